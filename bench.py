@@ -1,0 +1,293 @@
+"""Benchmark of one outer iteration of the memory-reduced iterative DVM scheme
+(arXiv 1810.00348) on the GB300, printed as one JSON line.
+
+Workload: the 3D lid-driven cavity with 64^3 uniform cells and 32^3 uniform
+velocities on [-4, 4]^3 (trapezoid weights), Shakhov Pr = 2/3, omega = 0.81,
+Kn = 1, lid speed 0.16 (synthetic problem definition, no dataset).  A step is
+one outer iteration: coefficients, all sweep stages with the fused
+equilibrium and moments, and the FP64 closure (moments -> macros, wall
+densities, mass rescale, residual).  The headline value is the mixed form
+(FP32 sweep and equilibrium, FP64 moment partials and closure); the plain
+FP64 form is measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on a bounded sample of the same workload.  Under torchrun each rank runs an
+independent replica of the workload (the solver is single-GPU; weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "phase-point updates/s"
+WORKLOAD = "3D lid-driven cavity 64^3 cells x 32^3 velocities, Kn=1, lid 0.16"
+N_CELL, N_VEL, KN, LID = 64, 32, 1.0, 0.16
+
+# Algorithmic FP32/FP64 operations per phase-point update in the sweep kernel
+# (FMA = 2): equilibrium of Eq. (2) 20 + exp 1; implicit update of Eq. (7)
+# 13 (with the division); 13 moment sums about U^n 34.
+FLOPS_PER_PP = 68
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of the GB300
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = str(gpu_index)
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def time_oracle_sample():
+    """Oracle (plain serial FP64 C) on a bounded sample of the workload: the
+    64^3-cell cavity with a 6^3 velocity grid (one outer iteration)."""
+    from oracle import Oracle
+    from paper_1810_00348_gb300 import inputs
+
+    prob = inputs.cavity(N_CELL, 6, Kn=KN, lid=LID)
+    o = Oracle(prob)
+    t0 = time.perf_counter()
+    o.iterate()
+    dt = time.perf_counter() - t0
+    pp = prob.phase_points()
+    return {"value": pp / dt, "unit": "phase-point updates/s", "cores": 1, "kind": "oracle",
+            "sample": "one outer iteration of the 64^3-cell cavity with a 6^3 velocity grid "
+                      "(%d phase points, %.1f s on one host core)" % (pp, dt)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    # the oracle is plain serial CPU code with no warm-up effects: every step
+    # is a timed sample
+    cb = time_oracle_sample()
+    vals = [cb["value"]]
+    for _ in range(max(args.steps - 1, 0)):
+        vals.append(time_oracle_sample()["value"])
+    v = statistics.median(vals)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "phase-point updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle sample: 6^3 velocities)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "phase-point updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1810_00348_gb300 import inputs, kgs
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    kgs.load()
+    prob = inputs.cavity(N_CELL, N_VEL, Kn=KN, lid=LID)
+    pp = prob.phase_points()
+    peaks = _peaks()
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def timed(ctx, steps):
+        kgs.kgs_profile(ctx)  # reset counters
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(steps):
+            rc, done, res = kgs.kgs_iterate(ctx, 1)
+            if rc != kgs.KGS_OK:
+                raise RuntimeError("kgs_iterate returned %d" % rc)
+        ev1.record()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        sweep_ms, sweep_launches, launches = kgs.kgs_profile(ctx)
+        if pg is not None:
+            t = torch.tensor([ms], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, sweep_ms, sweep_launches, launches
+
+    # ---- mixed precision (headline) ----
+    ctx = kgs.kgs_setup(prob, precision=kgs.KGS_MIXED, v_per_cta=args.v_per_cta, block_z=args.block_z)
+    kgs.kgs_set_profiling(ctx, True)
+    info = kgs.kgs_info(ctx)
+    kgs.kgs_iterate(ctx, args.warmup)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ms, sweep_ms, sweep_launches, launches = timed(ctx, args.steps)
+    clocks = sampler.stop()
+    value = pp * args.steps * world / (ms / 1e3)
+    ms_step = ms / args.steps
+    sweep_ms_iter = sweep_ms / args.steps
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    achieved = FLOPS_PER_PP * pp / (sweep_ms_iter / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "sweep_kernel<float>", "flops_per_phase_point": FLOPS_PER_PP,
+                "peak_basis": "FP32 FMA lanes: %d SMs x %d lanes x 2 x %.0f MHz (derived)" % (
+                    SM_COUNT, FP32_LANES_PER_SM, sm_mhz),
+                "sweep_ms_per_step": sweep_ms_iter, "sweep_share_of_step": sweep_ms_iter / ms_step}
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    state_bytes = kgs.kgs_save_size(ctx)
+    h_state = torch.empty(state_bytes, dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(8 * prob.ncell, dtype=torch.float64, pin_memory=True)
+    kgs.kgs_save_ptr(ctx, h_state.data_ptr(), state_bytes)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        kgs.kgs_load_ptr(ctx, h_state.data_ptr(), state_bytes)
+        kgs.kgs_iterate(ctx, 1)
+        kgs.kgs_moments_ptr(ctx, h_out.data_ptr())
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": pp * args.steps * world / e2e_s, "unit": "phase-point updates/s",
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": 8 * 8 * prob.ncell + 16,
+           "api": "kgs_load (state from pinned host) + kgs_iterate(1) + kgs_moments (to pinned host)"}
+    del ctx
+
+    # ---- plain FP64 beside it ----
+    fp64 = None
+    if not args.no_fp64:
+        c64 = kgs.kgs_setup(prob, precision=kgs.KGS_FP64, block_z=args.block_z)
+        kgs.kgs_set_profiling(c64, True)
+        kgs.kgs_iterate(c64, 1)
+        k64 = max(1, min(args.steps, 3))
+        ms64, sw64, _, _ = timed(c64, k64)
+        a64 = FLOPS_PER_PP * pp / (sw64 / k64 / 1e3) / 1e12
+        fp64 = {"value": pp * k64 * world / (ms64 / 1e3), "unit": "phase-point updates/s", "steps": k64,
+                "ms_per_step": ms64 / k64,
+                "roofline": {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": a64 / FP64_PEAK_TFLOPS, "peak_basis": "nominal dense FP64 1.25 TFLOP/s"}}
+        del c64
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": "phase-point updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweep / f64 moments", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": prob.ncell, "velocities": prob.nvel,
+                   "phase_points_per_step": pp, "precision": "mixed", "v_per_cta": info["v_per_cta"],
+                   "block_z": info["block_z"], "sweep_stages": info["n_stages"],
+                   "device_bytes": info["device_bytes"],
+                   "l2": "working set larger than L2 (face planes and moment partials, %.1f GB)" % (
+                       info["device_bytes"] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "fp64": fp64,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--v-per-cta", type=int, default=0)
+    ap.add_argument("--block-z", type=int, default=0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * kgs.h -- C ABI of the GB300 (sm_103a) solver for the steady Shakhov / BGK
+ * model equation by the memory-reduced iterative discrete velocity method of
+ * Zhu, Wang, Chen, Guo & Zhang (arXiv 1810.00348).
+ *
+ * One outer iteration (Eq. (6)) does, for every discrete velocity, the
+ * first-order upwind implicit sweep of Eq. (7) with the Shakhov equilibrium
+ * of Eq. (2) evaluated from the lagged macroscopic fields, adds the velocity's
+ * contribution to the quadrature moments of Eq. (5) and to the incoming wall
+ * fluxes of Eq. (9), and then closes with the macroscopic update, the wall
+ * densities, the global mass rescaling of Section 3.4 and the convergence
+ * monitor of Section 4.1.  The full phase-space distribution is never stored
+ * (Section 2.2 and Section 3.2 memory reduction): only one XY slice per
+ * in-flight velocity and the block faces between sweep stages.
+ *
+ * Units: lengths in the cavity side, velocities in sqrt(2 R T0), temperature
+ * in T0, density in rho0; the gas constant is R = 1/2 and p = rho R T.
+ *
+ * Layouts (all FP64 unless stated):
+ *   cell c = i + nx*(j + ny*k);
+ *   macroscopic fields  [8][nz][ny][nx]: rho, Ux, Uy, Uz, T, qx, qy, qz;
+ *   wall densities      [6][nz][ny][nx]: one value per cell face, sides
+ *                       -x, +x, -y, +y, -z, +z (0 where the face is not a wall);
+ *   discrete velocities a = ix + nvx*(iy + nvy*iz), xi_a = (xi_x[ix],
+ *                       xi_y[iy], xi_z[iz]), weight w_x[ix] w_y[iy] w_z[iz].
+ *
+ * Ownership: every input array is copied during the call that receives it;
+ * the caller keeps ownership.  Output arrays are caller-owned and must hold
+ * the stated number of elements.  The library allocates (cudaMalloc) and
+ * frees all of its device memory itself and launches on the stream given in
+ * kgs_opts (NULL = the legacy default stream) of the device that is current
+ * at kgs_setup.  One context must not be used by two host threads at once;
+ * distinct contexts are independent.  Results are deterministic: every
+ * reduction runs in a fixed order.
+ *
+ * Errors: functions return KGS_OK (0) or a negative KGS_E* code;
+ * kgs_iterate returns KGS_NOTCONVERGED (> 0) when its iteration budget ends
+ * above the tolerance.  kgs_strerror() gives a message.  After KGS_ECUDA the
+ * context should be destroyed.
+ */
+#ifndef KGS_H
+#define KGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KGS_OK 0
+#define KGS_NOTCONVERGED 1
+#define KGS_EINVAL (-1)     /* invalid argument                                   */
+#define KGS_ENOMEM (-2)     /* device or host allocation failed                    */
+#define KGS_ECUDA (-3)      /* a CUDA call failed                                  */
+#define KGS_EDIVERGED (-4)  /* NaN, rho <= 0 or T <= 0 after an iteration          */
+#define KGS_ETIMEOUT (-5)   /* a bounded device wait expired                       */
+#define KGS_EFORMAT (-6)    /* checkpoint buffer does not match this context       */
+
+enum { KGS_FACE_WALL = 0, KGS_FACE_INFLOW = 1 };
+enum { KGS_FP64 = 0, KGS_MIXED = 1 };
+enum { KGS_WALL_DISCRETE = 0, KGS_WALL_ANALYTIC = 1 };
+
+typedef struct kgs_ctx kgs_ctx;
+
+/* Physical grid: nx*ny*nz Cartesian cells with widths dx[nx], dy[ny], dz[nz]
+ * (Eq. (7) uses the width of the cell being updated). */
+typedef struct {
+    int nx, ny, nz;
+    const double *dx, *dy, *dz;
+} kgs_grid;
+
+/* Tensor-product velocity grid with its quadrature weights (Eq. (4), Eq. (5)).
+ * Nodes need not be uniform; a node at exactly 0 has no upwind dependence
+ * along that axis. */
+typedef struct {
+    int nvx, nvy, nvz;
+    const double *xi_x, *xi_y, *xi_z;
+    const double *w_x, *w_y, *w_z;
+} kgs_vgrid;
+
+/* Gas model: Knudsen number (Kn = +inf gives the free-molecular limit
+ * 1/tau = 0), Prandtl number (Pr = 2/3 Shakhov, Pr = 1 BGK), viscosity index
+ * omega of mu = mu_ref T^omega, mu_ref from Kn by Eq. (10) with the initial
+ * uniform state as reference (T_ref = 1, p_ref = 1/2). */
+typedef struct {
+    double Kn, Pr, omega;
+} kgs_gas;
+
+/* Boundaries (Section 3.4).  type[s] for domain side s (-x,+x,-y,+y,-z,+z):
+ * KGS_FACE_WALL = diffuse wall at T_w[s] moving at U_w[s] (Eq. (8), centred
+ * on the wall velocity), KGS_FACE_INFLOW = free-stream equilibrium
+ * (rho_in, U_in, T_in).  Faces between fluid and solid cells are diffuse
+ * walls at rest at T_solid. */
+typedef struct {
+    int type[6];
+    double T_w[6];
+    double U_w[6][3];
+    double rho_in, U_in[3], T_in;
+    double T_solid;
+} kgs_bc;
+
+/* Options.
+ *   precision    KGS_FP64: every step in FP64.  KGS_MIXED: equilibrium and
+ *                sweep in FP32, moment sums FP32 within a slice then FP64,
+ *                closure in FP64.
+ *   wall_norm    KGS_WALL_DISCRETE: rho_w = incoming flux / discrete outgoing
+ *                flux of the unit wall Maxwellian (zero discrete mass flux).
+ *                KGS_WALL_ANALYTIC: rho_w = sqrt(2 pi/(R T_w)) * incoming flux,
+ *                the printed Eq. (9) with the quadrature weights.
+ *   mass_rescale 1: rescale rho, q and rho_w each iteration so that the total
+ *                mass stays at its initial value (closed cavities, Section 3.4).
+ *   max_iters, tol  used by kgs_iterate(n_iters <= 0): iterate until the
+ *                residual is below tol or max_iters iterations have run.
+ *   v_per_cta    discrete velocities per thread block (0 = default for the
+ *                precision); block_z cells per sweep block along z (0 = default).
+ *   stream       cudaStream_t to launch on (NULL = legacy default stream). */
+typedef struct {
+    int precision;
+    int wall_norm;
+    int mass_rescale;
+    int max_iters;
+    double tol;
+    int v_per_cta;
+    int block_z;
+    void *stream;
+} kgs_opts;
+
+/* Sizes and counters of a context. */
+typedef struct {
+    int nx, ny, nz, nvx, nvy, nvz;
+    long long n_fluid;          /* fluid cells                                     */
+    long long phase_points;     /* n_fluid * nvel: updates per outer iteration     */
+    int iteration;              /* outer iterations done since setup / load        */
+    int n_stages;               /* sweep launches per outer iteration              */
+    int v_per_cta, block_z, precision;
+    size_t device_bytes;        /* device memory held by the context               */
+    double last_residual;
+} kgs_info_t;
+
+/* Build a context: copy the grids, mask and parameters to the device,
+ * precompute per-velocity tables and start from the uniform state (the free
+ * stream if any side is an inflow, else rho = 1, U = 0, T = 1, q = 0), with
+ * wall densities from the flux of that state's equilibrium.
+ * solid: nx*ny*nz bytes, 1 = solid cell, or NULL.
+ * Errors: KGS_EINVAL (sizes < 1, non-positive widths or weights, Pr or omega
+ * out of range, Kn = +inf together with a zero velocity node on every axis),
+ * KGS_ENOMEM, KGS_ECUDA. */
+int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vgrid,
+              const kgs_gas *gas, const kgs_bc *bc, const kgs_opts *opts);
+
+/* Replace the macroscopic fields (host [8][nz][ny][nx]; NULL = the uniform
+ * state of kgs_setup) and recompute the wall densities from the flux of the
+ * new equilibrium (Section 2.2: the iteration starts from f^{S,0}).  Resets
+ * the iteration counter and the reference mass used by mass_rescale. */
+int kgs_set_initial(kgs_ctx *ctx, const double *macros);
+
+/* Run outer iterations.  n_iters > 0: exactly n_iters iterations.
+ * n_iters <= 0: until residual < opts.tol or opts.max_iters iterations.
+ * *done (may be NULL) receives the number of iterations run, *residual
+ * (may be NULL) the last residual (Section 4.1 reading: the largest relative
+ * L2 change of rho, rho Ux, rho Uy, rho Uz, rho E over fluid cells, each
+ * denominator floored at 1e-8 ||rho||_2).
+ * Returns KGS_OK, KGS_NOTCONVERGED (n_iters <= 0 only), KGS_EDIVERGED
+ * (the state is left at the offending iterate), KGS_ECUDA. */
+int kgs_iterate(kgs_ctx *ctx, int n_iters, int *done, double *residual);
+
+/* Copy the current macroscopic fields to host memory out[8*nz*ny*nx]
+ * (solid cells hold 0).  Synchronises the context's stream. */
+int kgs_moments(kgs_ctx *ctx, double *out);
+
+/* Same, into device memory out_dev[8*nz*ny*nx] on the context's device;
+ * asynchronous on the context's stream. */
+int kgs_moments_device(kgs_ctx *ctx, double *out_dev);
+
+/* Wall densities, host out[6*nz*ny*nx] (see the layout above). */
+int kgs_rho_w(kgs_ctx *ctx, double *out);
+
+/* Overwrite the wall densities (host in[6*nz*ny*nx]); entries of faces that
+ * are not walls are ignored. */
+int kgs_set_rho_w(kgs_ctx *ctx, const double *in);
+
+/* Checkpoint.  The whole solver state is the macroscopic fields, the wall
+ * densities, the reference mass and the iteration counter (the distribution
+ * is never stored).  kgs_save with buf = NULL sets *len to the size needed;
+ * otherwise it writes *len bytes.  kgs_load restores a buffer written by a
+ * context of the same sizes (KGS_EFORMAT otherwise); iterating after a load
+ * reproduces an uninterrupted run bit for bit. */
+int kgs_save(kgs_ctx *ctx, void *buf, size_t *len);
+int kgs_load(kgs_ctx *ctx, const void *buf, size_t len);
+
+int kgs_info(kgs_ctx *ctx, kgs_info_t *out);
+
+/* Sweep-kernel timing for roofline reports: when enabled, CUDA events are
+ * recorded on the context's stream around every sweep launch; kgs_profile
+ * returns the summed device time (ms) and the number of sweep launches since
+ * the last reset, and resets the counters.  Synchronises the stream. */
+int kgs_set_profiling(kgs_ctx *ctx, int enable);
+int kgs_profile(kgs_ctx *ctx, double *sweep_ms, long long *sweep_launches, long long *kernel_launches);
+
+void kgs_destroy(kgs_ctx *ctx);
+const char *kgs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

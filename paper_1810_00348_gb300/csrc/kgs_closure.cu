@@ -1,0 +1,330 @@
+// kgs_closure.cu -- per-iteration kernels around the sweep (arXiv 1810.00348):
+//   coef_kernel      lagged cell coefficients of Eq. (2) and tau = mu/p (Eq. (10))
+//   close_kernel     fixed-order sum of the per-group partials, the macroscopic
+//                    update of Eq. (5) and the wall densities of Eq. (9)
+//   finalize_mass    global mass and the Section 3.4 rescale factor
+//   scale_residual   rescale, divergence check and the Section 4.1 residual
+//   finalize_residual
+//   wall_flux_init   wall densities from the flux of the initial equilibrium
+// All arithmetic in FP64.  Every reduction is a fixed-shape tree per block
+// followed by an in-order sum over blocks, so results do not depend on
+// scheduling.
+#include "kgs_internal.h"
+
+namespace kgs {
+namespace {
+
+constexpr double R_GAS = 0.5;
+constexpr double LOG2E = 1.4426950408889634074;
+constexpr int RED_THREADS = 256;
+
+template <typename Real>
+__global__ void coef_kernel(const double *__restrict__ mac, const uint8_t *__restrict__ solid,
+                            const uint8_t *__restrict__ side_flags, const double *__restrict__ rdx,
+                            const double *__restrict__ rdy, const double *__restrict__ rdz, int nx, int ny, int nz,
+                            double mu_ref, double omega, double Pr, Real *__restrict__ coef)
+{
+    const size_t ncell = (size_t)nx * ny * nz;
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((size_t)nx * ny));
+    Real out[NCOEF];
+    for (int q = 0; q < NCOEF; q++) out[q] = Real(0);
+    const int sf = side_flags[c];  // bits 0..5 solid neighbour, 6..11 wall face (packed in 2 bytes)
+    const int wf = side_flags[ncell + c];
+    int flags = ((sf & 63) * F_SOLID_SIDE) | ((wf & 63) << 7);
+    if (solid && solid[c]) {
+        flags |= F_SOLID;
+    } else {
+        const double rho = mac[c], T = mac[4 * ncell + c];
+        const double RT = R_GAS * T;
+        const double p = rho * RT;
+        // tau = mu / p, mu = mu_ref T^omega (Sections 2.1 and 4)
+        const double rtau = p / (mu_ref * pow(T, omega));
+        const double A = rho / pow(2.0 * M_PI * RT, 1.5);
+        const double sh = (1.0 - Pr) / (5.0 * p * RT);
+        out[C_UX] = (Real)mac[1 * ncell + c];
+        out[C_UY] = (Real)mac[2 * ncell + c];
+        out[C_UZ] = (Real)mac[3 * ncell + c];
+        out[C_KAPPA] = (Real)(rtau * A);
+        out[C_NEXP] = sizeof(Real) == 8 ? (Real)(-1.0 / (2.0 * RT)) : (Real)(-LOG2E / (2.0 * RT));
+        out[C_RT1] = (Real)(1.0 / RT);
+        out[C_QX] = (Real)(sh * mac[5 * ncell + c]);
+        out[C_QY] = (Real)(sh * mac[6 * ncell + c]);
+        out[C_QZ] = (Real)(sh * mac[7 * ncell + c]);
+        out[C_RTAU] = (Real)rtau;
+        out[C_RDX] = (Real)rdx[i];
+        out[C_RDY] = (Real)rdy[j];
+        out[C_RDZ] = (Real)rdz[k];
+    }
+    out[C_FLAGS] = (Real)flags;
+    for (int q = 0; q < NCOEF; q++) coef[c * NCOEF + q] = out[q];
+}
+
+// Block tree sum of NV doubles per thread into blk[blockIdx.x * NV + v].
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *blk)
+{
+    __shared__ double sh[NV][RED_THREADS];
+    for (int q = 0; q < NV; q++) sh[q][threadIdx.x] = v[q];
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int q = 0; q < NV; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < NV; q++) blk[(size_t)blockIdx.x * NV + q] = sh[q][0];
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(RED_THREADS) close_kernel(const CloseArgs a)
+{
+    const size_t ncell = a.ncell;
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double mass[1] = {0.0};
+    if (c < ncell && !(a.solid && a.solid[c])) {
+        double S[13];
+        double F[6] = {0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < 13; q++) S[q] = 0.0;
+        for (int g = 0; g < a.n_vg; g++) {
+            const double *pp = a.part + (size_t)g * NPART * ncell + c;
+            for (int q = 0; q < 13; q++) S[q] += pp[(size_t)q * ncell];
+            const int o = a.vg_oct[g];
+            // incoming flux onto the wall ahead of the octant along each axis
+            F[(o & 1) ? 1 : 0] += pp[(size_t)P_FX * ncell];
+            F[(o & 2) ? 3 : 2] += pp[(size_t)P_FY * ncell];
+            F[(o & 4) ? 5 : 4] += pp[(size_t)P_FZ * ncell];
+        }
+        const Real *cf = static_cast<const Real *>(a.coef) + c * NCOEF;
+        // The sums were taken about the lagged velocity U^n as stored in the
+        // sweep precision; shift exactly to U^{n+1} = U^n + delta.
+        const double Uc[3] = {(double)cf[C_UX], (double)cf[C_UY], (double)cf[C_UZ]};
+        const double rho = S[P_S0];
+        const double d[3] = {S[P_S1X] / rho, S[P_S1Y] / rho, S[P_S1Z] / rho};
+        const double S2[3][3] = {{S[P_S2XX], S[P_S2XY], S[P_S2XZ]},
+                                 {S[P_S2XY], S[P_S2YY], S[P_S2YZ]},
+                                 {S[P_S2XZ], S[P_S2YZ], S[P_S2ZZ]}};
+        const double S1[3] = {S[P_S1X], S[P_S1Y], S[P_S1Z]};
+        const double S3[3] = {S[P_S3X], S[P_S3Y], S[P_S3Z]};
+        const double trS2 = S2[0][0] + S2[1][1] + S2[2][2];
+        const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const double dS1 = d[0] * S1[0] + d[1] * S1[1] + d[2] * S1[2];
+        // rho E - rho |U|^2 / 2 = tr(P)/2 with P = S2 - S0 delta delta^T, and
+        // rho E = rho |U|^2/2 + (3/2) rho R T (Section 2.1)
+        const double trP = trS2 - rho * d2;
+        const double T = trP / (3.0 * rho * R_GAS);
+        double q[3];
+        for (int i = 0; i < 3; i++) {
+            // q_i = 1/2 sum w f (c'-delta)_i |c'-delta|^2 expanded in the sums about U^n
+            const double S2d = S2[i][0] * d[0] + S2[i][1] * d[1] + S2[i][2] * d[2];
+            q[i] = 0.5 * (S3[i] - 2.0 * S2d - d[i] * trS2 + 2.0 * d[i] * dS1 + d2 * S1[i] - rho * d2 * d[i]);
+        }
+        double *mn = a.mac_new;
+        mn[c] = rho;
+        mn[1 * ncell + c] = Uc[0] + d[0];
+        mn[2 * ncell + c] = Uc[1] + d[1];
+        mn[3 * ncell + c] = Uc[2] + d[2];
+        mn[4 * ncell + c] = T;
+        mn[5 * ncell + c] = q[0];
+        mn[6 * ncell + c] = q[1];
+        mn[7 * ncell + c] = q[2];
+        for (int s = 0; s < 6; s++) {
+            const int kind = a.wall_kind[s * ncell + c];
+            a.rho_w_new[s * ncell + c] = kind >= 0 ? F[s] * a.wall_norm[kind * 6 + s] : 0.0;
+        }
+        const int i = (int)(c % a.nx), j = (int)((c / a.nx) % a.ny), k = (int)(c / ((size_t)a.nx * a.ny));
+        mass[0] = rho * a.dx[i] * a.dy[j] * a.dz[k];
+    } else if (c < ncell) {
+        for (int q = 0; q < 8; q++) a.mac_new[q * ncell + c] = 0.0;
+        for (int s = 0; s < 6; s++) a.rho_w_new[s * ncell + c] = 0.0;
+    }
+    block_sum<1>(mass, a.blk_mass);
+}
+
+__global__ void finalize_mass_kernel(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double M = 0.0;
+    for (int b = 0; b < n_blocks; b++) M += blk_mass[b];
+    scale[0] = rescale ? M0 / M : 1.0;
+    scale[1] = M;
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    scale_residual_kernel(double *mac_new, double *rho_w_new, const double *mac, const uint8_t *solid, size_t ncell,
+                          const double *scale, double *blk_res, int *blk_bad)
+{
+    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double s = scale[0];
+    double v[10];
+    for (int q = 0; q < 10; q++) v[q] = 0.0;
+    int bad = 0;
+    if (c < ncell && !(solid && solid[c])) {
+        mac_new[c] *= s;
+        for (int d = 0; d < 3; d++) mac_new[(5 + d) * ncell + c] *= s;
+        for (int f = 0; f < 6; f++) rho_w_new[f * ncell + c] *= s;
+        double pn[5], po[5];
+        for (int t = 0; t < 2; t++) {
+            const double *m = t ? mac : mac_new;
+            double *phi = t ? po : pn;
+            const double r = m[c], ux = m[ncell + c], uy = m[2 * ncell + c], uz = m[3 * ncell + c],
+                         T = m[4 * ncell + c];
+            phi[0] = r;
+            phi[1] = r * ux;
+            phi[2] = r * uy;
+            phi[3] = r * uz;
+            phi[4] = 0.5 * r * (ux * ux + uy * uy + uz * uz) + 1.5 * r * R_GAS * T;
+        }
+        for (int t = 0; t < 5; t++) {
+            const double dd = pn[t] - po[t];
+            v[t] = dd * dd;
+            v[5 + t] = pn[t] * pn[t];
+        }
+        const double r = mac_new[c], T = mac_new[4 * ncell + c];
+        bool finite = isfinite(r) && isfinite(T);
+        for (int q = 1; q < 8; q++) finite = finite && isfinite(mac_new[q * ncell + c]);
+        if (!(r > 0.0) || !(T > 0.0) || !finite) bad = 1;
+    }
+    block_sum<10>(v, blk_res);
+    __shared__ int any_bad;
+    if (threadIdx.x == 0) any_bad = 0;
+    __syncthreads();
+    if (bad) any_bad = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) blk_bad[blockIdx.x] = any_bad;
+}
+
+__global__ void finalize_residual_kernel(const double *blk_res, const int *blk_bad, int n_blocks, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double dn[5] = {0, 0, 0, 0, 0}, nn[5] = {0, 0, 0, 0, 0};
+    int bad = 0;
+    for (int b = 0; b < n_blocks; b++) {
+        for (int t = 0; t < 5; t++) {
+            dn[t] += blk_res[(size_t)b * 10 + t];
+            nn[t] += blk_res[(size_t)b * 10 + 5 + t];
+        }
+        bad |= blk_bad[b];
+    }
+    // Section 4.1 reading: largest relative L2 change over rho, rho U, rho E;
+    // denominators floored at 1e-8 ||rho||_2.
+    double res = 0.0;
+    const double fl = 1e-8 * sqrt(nn[0]);
+    for (int t = 0; t < 5; t++) {
+        double den = sqrt(nn[t]);
+        if (den < fl) den = fl;
+        const double r = sqrt(dn[t]) / den;
+        if (r > res) res = r;
+    }
+    out[0] = res;
+    out[1] = bad ? 1.0 : 0.0;
+}
+
+// rho_w^0 from the flux of f^{S,0}: one thread per (side, cell) wall face.
+__global__ void wall_flux_init_kernel(const double *mac, const int8_t *wall_kind, const double *wall_norm,
+                                      const double *vel64, int Nv, size_t ncell, double R, double Pr,
+                                      double *rho_w)
+{
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 6 * ncell) return;
+    const int s = (int)(idx / ncell);
+    const size_t c = idx % ncell;
+    const int kind = wall_kind[idx];
+    if (kind < 0) {
+        rho_w[idx] = 0.0;
+        return;
+    }
+    const double rho = mac[c], T = mac[4 * ncell + c];
+    const double U[3] = {mac[ncell + c], mac[2 * ncell + c], mac[3 * ncell + c]};
+    const double q[3] = {mac[5 * ncell + c], mac[6 * ncell + c], mac[7 * ncell + c]};
+    const double RT = R * T, p = rho * RT;
+    const double A = rho / pow(2.0 * M_PI * RT, 1.5);
+    const int d = s / 2;
+    const double nrm = (s % 2) ? -1.0 : 1.0;  // normal from the wall into the gas
+    double F = 0.0;
+    for (int g = 0; g < Nv; g++) {
+        const double *v = vel64 + (size_t)g * 4;
+        const double xn = v[d] * nrm;
+        if (!(xn < 0.0)) continue;
+        const double cx = v[0] - U[0], cy = v[1] - U[1], cz = v[2] - U[2];
+        const double c2 = cx * cx + cy * cy + cz * cz;
+        const double cq = cx * q[0] + cy * q[1] + cz * q[2];
+        const double fS = A * exp(-c2 / (2.0 * RT)) * (1.0 + (1.0 - Pr) * cq / (5.0 * p * RT) * (c2 / RT - 5.0));
+        F += v[3] * (-xn) * fS;
+    }
+    rho_w[idx] = F * wall_norm[kind * 6 + s];
+}
+
+__global__ void fill_kernel(double *p, size_t n, double v)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, const uint8_t *side_flags,
+                        const double *rdx, const double *rdy, const double *rdz, int nx, int ny, int nz,
+                        double mu_ref, double omega, double Pr, void *coef, cudaStream_t s)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    if (precision == 0)
+        coef_kernel<double><<<nblk(n, 256), 256, 0, s>>>(mac, solid, side_flags, rdx, rdy, rdz, nx, ny, nz, mu_ref,
+                                                          omega, Pr, static_cast<double *>(coef));
+    else
+        coef_kernel<float><<<nblk(n, 256), 256, 0, s>>>(mac, solid, side_flags, rdx, rdy, rdz, nx, ny, nz, mu_ref,
+                                                         omega, Pr, static_cast<float *>(coef));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_close(const CloseArgs &a, int n_blocks, cudaStream_t s)
+{
+    if (a.precision == 0)
+        close_kernel<double><<<n_blocks, RED_THREADS, 0, s>>>(a);
+    else
+        close_kernel<float><<<n_blocks, RED_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_mass(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale,
+                                 cudaStream_t s)
+{
+    finalize_mass_kernel<<<1, 32, 0, s>>>(blk_mass, n_blocks, M0, rescale, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_residual(double *mac_new, double *rho_w_new, const double *mac, const uint8_t *solid,
+                                  unsigned long long ncell, const double *scale, double *blk_res, int *blk_bad,
+                                  int n_blocks, cudaStream_t s)
+{
+    scale_residual_kernel<<<n_blocks, RED_THREADS, 0, s>>>(mac_new, rho_w_new, mac, solid, ncell, scale, blk_res,
+                                                           blk_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_residual(const double *blk_res, const int *blk_bad, int n_blocks, double *out2,
+                                     cudaStream_t s)
+{
+    finalize_residual_kernel<<<1, 32, 0, s>>>(blk_res, blk_bad, n_blocks, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_flux_init(const double *mac, const int8_t *wall_kind, const double *wall_norm,
+                                  const double *vel64, int Nv, unsigned long long ncell, double R, double Pr,
+                                  double *rho_w, cudaStream_t s)
+{
+    wall_flux_init_kernel<<<nblk(6 * ncell, 128), 128, 0, s>>>(mac, wall_kind, wall_norm, vel64, Nv, ncell, R, Pr,
+                                                                rho_w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double *p, unsigned long long n, double v, cudaStream_t s)
+{
+    fill_kernel<<<nblk(n, 256), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+}  // namespace kgs

@@ -1,0 +1,112 @@
+// kgs_internal.h -- device-side data layouts and launch interfaces shared by
+// the CUDA translation units of libkgs.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kgs {
+
+// Spatial sweep block: BX x BY cells in the XY plane (compile time), a
+// run-time number of cells along z.  The XY slice of every in-flight velocity
+// stays in shared memory while the block marches along z (Section 3.2's slice
+// marching, one slice updated in place).
+constexpr int BX = 8;
+constexpr int BY = 8;
+constexpr int SLICE = BX * BY;
+constexpr int NT = 128;          // threads per sweep CTA
+constexpr int NCOEF = 16;        // per-cell coefficient record
+constexpr int NPART = 16;        // per-cell partial: 13 moment sums + 3 wall fluxes
+
+// Per-cell coefficient record (computed from the lagged FP64 macros each
+// iteration, stored in the sweep precision).
+enum {
+    C_UX = 0, C_UY, C_UZ,   // lagged velocity U^n: centre of c = xi - U^n
+    C_KAPPA,                // (1/tau) rho (2 pi R T)^{-3/2}
+    C_NEXP,                 // exponent scale: -1/(2RT) (FP64) or -log2(e)/(2RT) (FP32)
+    C_RT1,                  // 1/(R T)
+    C_QX, C_QY, C_QZ,       // (1 - Pr) q / (5 p R T)
+    C_RTAU,                 // 1/tau
+    C_RDX, C_RDY, C_RDZ,    // 1/dx_i, 1/dy_j, 1/dz_k
+    C_FLAGS,                // cell flags (below), stored as a small integer value
+    C_PAD0, C_PAD1
+};
+
+// Cell flags.
+constexpr int F_SOLID = 1;               // the cell itself is solid
+constexpr int F_SOLID_SIDE = 2;          // << s: the neighbour on side s is solid
+constexpr int F_WALL_SIDE = 1 << 7;      // << s: face on side s is a diffuse wall
+
+// Partial-sum slots per (velocity group, cell): the 13 sums about U^n
+// (S0, S1xyz, S2 xx yy zz xy xz yz, S3xyz) and the incoming flux onto the
+// wall ahead of the octant along x, y, z.
+enum {
+    P_S0 = 0, P_S1X, P_S1Y, P_S1Z, P_S2XX, P_S2YY, P_S2ZZ, P_S2XY, P_S2XZ, P_S2YZ,
+    P_S3X, P_S3Y, P_S3Z, P_FX, P_FY, P_FZ
+};
+
+// Wall-Maxwellian table rows: 0..5 domain side, 6 solid surface, 7 free stream.
+constexpr int MT_SOLID = 6;
+constexpr int MT_INFLOW = 7;
+constexpr int MT_ROWS = 8;
+
+struct SweepArgs {
+    int nx, ny, nz, bz;           // grid, block extent along z
+    int nbx, nby, nbz;            // blocks per axis
+    const int4 *work;             // per CTA row: octant, reflected block coords
+    const int *oct_vstart;        // [8] first sorted velocity of each octant
+    const int *oct_vcount;        // [8] velocities per octant
+    const int *oct_vgbase;        // [8] first global velocity-group index
+    int Nv;                       // all velocities
+    int vg_size;                  // velocities per CTA
+    const void *vel;              // Real[Nv][4]: xi_x, xi_y, xi_z, w (octant-sorted)
+    const void *velw;             // Real[Nv][2]: w_x, w_y * w_z (tensor-product factors of w)
+    int oct_nx[8];                // x nodes in each octant (length of its velocity x-lines)
+    const void *coef;             // Real[ncell][NCOEF]
+    const double *rho_w;          // [6][ncell]
+    const void *mtab;             // Real[MT_ROWS][Nv]: unit wall Maxwellians, free stream
+    int side_inflow[6];           // domain side s is a free-stream boundary
+    void *FX, *FY, *FZ;           // face planes: [nz*ny][Nv], [nz*nx][Nv], [ny*nx][Nv]
+    double *part;                 // [n_vg][NPART][ncell]
+    unsigned long long ncell;
+};
+
+// Sweep launch (one wavefront stage).  precision: 0 FP64, 1 FP32.
+cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s);
+size_t sweep_smem_bytes(int precision, int tv);
+
+struct CloseArgs {
+    int nx, ny, nz;
+    unsigned long long ncell;
+    int n_vg;
+    const int *vg_oct;            // [n_vg] octant of each velocity group
+    const double *part;           // [n_vg][NPART][ncell]
+    const void *coef;             // sweep-precision coefficients (U centre)
+    int precision;
+    const double *mac;            // [8][ncell] step n
+    double *mac_new;              // [8][ncell] step n+1 (before rescale)
+    double *rho_w_new;            // [6][ncell]
+    const int8_t *wall_kind;      // [6][ncell]: -1 not a wall, 0..6 wall kind
+    const double *wall_norm;      // [7][6] rho_w = F * wall_norm[kind][side]
+    const double *dx, *dy, *dz;
+    const uint8_t *solid;         // [ncell] or NULL
+    double *blk_mass;             // [n_blocks]
+};
+
+cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, const uint8_t *cell_flags_side,
+                        const double *rdx, const double *rdy, const double *rdz, int nx, int ny, int nz,
+                        double mu_ref, double omega, double Pr, void *coef, cudaStream_t s);
+cudaError_t launch_close(const CloseArgs &a, int n_blocks, cudaStream_t s);
+cudaError_t launch_finalize_mass(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale,
+                                 cudaStream_t s);
+cudaError_t launch_scale_residual(double *mac_new, double *rho_w_new, const double *mac, const uint8_t *solid,
+                                  unsigned long long ncell, const double *scale, double *blk_res, int *blk_bad,
+                                  int n_blocks, cudaStream_t s);
+cudaError_t launch_finalize_residual(const double *blk_res, const int *blk_bad, int n_blocks, double *out2,
+                                     cudaStream_t s);
+cudaError_t launch_wall_flux_init(const double *mac, const int8_t *wall_kind, const double *wall_norm,
+                                  const double *vel64, int Nv, unsigned long long ncell, double R, double Pr,
+                                  double *rho_w, cudaStream_t s);
+cudaError_t launch_fill(double *p, unsigned long long n, double v, cudaStream_t s);
+
+}  // namespace kgs

@@ -1,0 +1,279 @@
+"""ctypes binding of libkgs.so (include/kgs.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels; there is no
+Python or CPU fallback.  If libkgs.so has not been built (``python -m
+paper_1810_00348_gb300.build``) or no CUDA device is usable, the calls fail
+with an exception.
+
+The function names follow the C ABI: ``kgs_setup``, ``kgs_set_initial``,
+``kgs_iterate``, ``kgs_moments``, ``kgs_moments_device``, ``kgs_rho_w``,
+``kgs_set_rho_w``, ``kgs_save``, ``kgs_load``, ``kgs_info``,
+``kgs_set_profiling``, ``kgs_profile``, ``kgs_destroy``, ``kgs_strerror``.
+Problems come from ``paper_1810_00348_gb300.inputs.Problem``.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkgs.so")
+
+KGS_OK = 0
+KGS_NOTCONVERGED = 1
+KGS_EINVAL = -1
+KGS_ENOMEM = -2
+KGS_ECUDA = -3
+KGS_EDIVERGED = -4
+KGS_ETIMEOUT = -5
+KGS_EFORMAT = -6
+KGS_FP64 = 0
+KGS_MIXED = 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class KgsGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", _dp), ("dy", _dp), ("dz", _dp)]
+
+
+class KgsVgrid(ctypes.Structure):
+    _fields_ = [("nvx", ctypes.c_int), ("nvy", ctypes.c_int), ("nvz", ctypes.c_int),
+                ("xi_x", _dp), ("xi_y", _dp), ("xi_z", _dp), ("w_x", _dp), ("w_y", _dp), ("w_z", _dp)]
+
+
+class KgsGas(ctypes.Structure):
+    _fields_ = [("Kn", ctypes.c_double), ("Pr", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class KgsBc(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int * 6), ("T_w", ctypes.c_double * 6), ("U_w", (ctypes.c_double * 3) * 6),
+                ("rho_in", ctypes.c_double), ("U_in", ctypes.c_double * 3), ("T_in", ctypes.c_double),
+                ("T_solid", ctypes.c_double)]
+
+
+class KgsOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("wall_norm", ctypes.c_int), ("mass_rescale", ctypes.c_int),
+                ("max_iters", ctypes.c_int), ("tol", ctypes.c_double), ("v_per_cta", ctypes.c_int),
+                ("block_z", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class KgsInfo(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("nvx", ctypes.c_int), ("nvy", ctypes.c_int), ("nvz", ctypes.c_int),
+                ("n_fluid", ctypes.c_longlong), ("phase_points", ctypes.c_longlong),
+                ("iteration", ctypes.c_int), ("n_stages", ctypes.c_int),
+                ("v_per_cta", ctypes.c_int), ("block_z", ctypes.c_int), ("precision", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t), ("last_residual", ctypes.c_double)]
+
+
+# exported symbols and their C signatures (restype, argtypes)
+SIGNATURES = {
+    "kgs_setup": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(KgsGrid),
+                                 ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(KgsVgrid), ctypes.POINTER(KgsGas),
+                                 ctypes.POINTER(KgsBc), ctypes.POINTER(KgsOpts)]),
+    "kgs_set_initial": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "kgs_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]),
+    "kgs_moments": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "kgs_moments_device": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "kgs_rho_w": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "kgs_set_rho_w": (ctypes.c_int, [ctypes.c_void_p, _dp]),
+    "kgs_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "kgs_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "kgs_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KgsInfo)]),
+    "kgs_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "kgs_profile": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)]),
+    "kgs_destroy": (None, [ctypes.c_void_p]),
+    "kgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+class KgsError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, load().kgs_strerror(code).decode(), code))
+
+
+def load(path: str = LIB_PATH):
+    """Load libkgs.so and declare every exported signature."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libkgs.so is not built (run python -m paper_1810_00348_gb300.build)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc, where, allow=()):
+    if rc != KGS_OK and rc not in allow:
+        raise KgsError(rc, where)
+    return rc
+
+
+def _arr(x, dtype=np.float64):
+    return np.ascontiguousarray(np.asarray(x, dtype=dtype))
+
+
+class Context:
+    """Handle of one kgs_ctx (one problem on the current CUDA device)."""
+
+    def __init__(self, handle, prob, keep):
+        self.handle = handle
+        self.prob = prob
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            kgs_destroy(self)
+
+    @property
+    def shape(self):
+        return (self.prob.nz, self.prob.ny, self.prob.nx)
+
+
+def kgs_setup(prob, precision=KGS_FP64, max_iters=1000, tol=1e-8, v_per_cta=0, block_z=0, stream=None):
+    """kgs_setup for an ``inputs.Problem``; stream is a cudaStream_t value (int) or None."""
+    lib = load()
+    keep = []
+
+    def p(a):
+        a = _arr(a)
+        keep.append(a)
+        return a.ctypes.data_as(_dp)
+
+    g = KgsGrid(prob.nx, prob.ny, prob.nz, p(prob.dx), p(prob.dy), p(prob.dz))
+    v = KgsVgrid(len(prob.xi_x), len(prob.xi_y), len(prob.xi_z), p(prob.xi_x), p(prob.xi_y), p(prob.xi_z),
+                 p(prob.w_x), p(prob.w_y), p(prob.w_z))
+    gas = KgsGas(prob.Kn, prob.Pr, prob.omega)
+    bc = KgsBc()
+    for s in range(6):
+        bc.type[s] = int(prob.face_type[s])
+        bc.T_w[s] = float(prob.T_w[s])
+        for d in range(3):
+            bc.U_w[s][d] = float(prob.U_w[s][d])
+    bc.rho_in, bc.T_in, bc.T_solid = prob.rho_in, prob.T_in, prob.T_solid
+    for d in range(3):
+        bc.U_in[d] = float(prob.U_in[d])
+    opts = KgsOpts(precision, int(prob.wall_mode), int(prob.mass_rescale), max_iters, tol, v_per_cta, block_z,
+                   ctypes.c_void_p(stream) if stream else None)
+    solid_p = ctypes.POINTER(ctypes.c_uint8)()
+    if prob.solid is not None:
+        sol = _arr(prob.solid, np.uint8).reshape(-1)
+        keep.append(sol)
+        solid_p = sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    h = ctypes.c_void_p()
+    _check(lib.kgs_setup(ctypes.byref(h), ctypes.byref(g), solid_p, ctypes.byref(v), ctypes.byref(gas),
+                         ctypes.byref(bc), ctypes.byref(opts)), "kgs_setup")
+    return Context(h, prob, None)
+
+
+def kgs_set_initial(ctx, macros=None):
+    if macros is None:
+        return _check(load().kgs_set_initial(ctx.handle, _dp()), "kgs_set_initial")
+    m = _arr(macros).reshape(-1)
+    return _check(load().kgs_set_initial(ctx.handle, m.ctypes.data_as(_dp)), "kgs_set_initial")
+
+
+def kgs_iterate(ctx, n_iters=1):
+    """Returns (rc, iterations_done, residual); KGS_NOTCONVERGED and
+    KGS_EDIVERGED are returned, other errors raise."""
+    done = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    rc = load().kgs_iterate(ctx.handle, int(n_iters), ctypes.byref(done), ctypes.byref(res))
+    _check(rc, "kgs_iterate", allow=(KGS_NOTCONVERGED, KGS_EDIVERGED))
+    return rc, done.value, res.value
+
+
+def kgs_moments(ctx, out=None):
+    n = ctx.prob.ncell
+    if out is None:
+        out = np.empty(8 * n)
+    _check(load().kgs_moments(ctx.handle, out.ctypes.data_as(_dp)), "kgs_moments")
+    return out.reshape((8,) + ctx.shape)
+
+
+def kgs_moments_device(ctx, dev_ptr):
+    return _check(load().kgs_moments_device(ctx.handle, ctypes.c_void_p(dev_ptr)), "kgs_moments_device")
+
+
+def kgs_rho_w(ctx):
+    out = np.empty(6 * ctx.prob.ncell)
+    _check(load().kgs_rho_w(ctx.handle, out.ctypes.data_as(_dp)), "kgs_rho_w")
+    return out.reshape((6,) + ctx.shape)
+
+
+def kgs_set_rho_w(ctx, rho_w):
+    a = _arr(rho_w).reshape(-1)
+    return _check(load().kgs_set_rho_w(ctx.handle, a.ctypes.data_as(_dp)), "kgs_set_rho_w")
+
+
+def kgs_save(ctx):
+    n = ctypes.c_size_t(0)
+    _check(load().kgs_save(ctx.handle, None, ctypes.byref(n)), "kgs_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().kgs_save(ctx.handle, buf, ctypes.byref(n)), "kgs_save")
+    return buf.raw[: n.value]
+
+
+def kgs_load(ctx, data: bytes):
+    buf = ctypes.create_string_buffer(data, len(data))
+    return load().kgs_load(ctx.handle, buf, len(data))
+
+
+def kgs_info(ctx):
+    info = KgsInfo()
+    _check(load().kgs_info(ctx.handle, ctypes.byref(info)), "kgs_info")
+    return {name: getattr(info, name) for name, _ in KgsInfo._fields_}
+
+
+def kgs_set_profiling(ctx, enable=True):
+    return _check(load().kgs_set_profiling(ctx.handle, 1 if enable else 0), "kgs_set_profiling")
+
+
+def kgs_profile(ctx):
+    ms = ctypes.c_double(0.0)
+    sl = ctypes.c_longlong(0)
+    kl = ctypes.c_longlong(0)
+    _check(load().kgs_profile(ctx.handle, ctypes.byref(ms), ctypes.byref(sl), ctypes.byref(kl)), "kgs_profile")
+    return ms.value, sl.value, kl.value
+
+
+def kgs_destroy(ctx):
+    if ctx.handle:
+        load().kgs_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def kgs_strerror(code):
+    return load().kgs_strerror(int(code)).decode()
+
+
+# ---- raw-pointer variants (pinned host or device buffers owned by the caller) ----
+
+def kgs_save_ptr(ctx, ptr, nbytes):
+    n = ctypes.c_size_t(nbytes)
+    _check(load().kgs_save(ctx.handle, ctypes.c_void_p(ptr), ctypes.byref(n)), "kgs_save")
+    return n.value
+
+
+def kgs_save_size(ctx):
+    n = ctypes.c_size_t(0)
+    _check(load().kgs_save(ctx.handle, None, ctypes.byref(n)), "kgs_save")
+    return n.value
+
+
+def kgs_load_ptr(ctx, ptr, nbytes):
+    return _check(load().kgs_load(ctx.handle, ctypes.c_void_p(ptr), nbytes), "kgs_load")
+
+
+def kgs_moments_ptr(ctx, ptr):
+    return _check(load().kgs_moments(ctx.handle, ctypes.cast(ctypes.c_void_p(ptr), _dp)), "kgs_moments")
