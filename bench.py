@@ -165,9 +165,11 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     kgs.load()
-    prob = inputs.cavity(N_CELL, N_VEL, Kn=KN, lid=LID)
+    prob = inputs.cavity(args.cells, args.vels, Kn=KN, lid=LID)
     pp = prob.phase_points()
     peaks = _peaks()
+    workload = WORKLOAD if (args.cells, args.vels) == (N_CELL, N_VEL) else \
+        "3D lid-driven cavity %d^3 cells x %d^3 velocities, Kn=1, lid 0.16" % (args.cells, args.vels)
 
     def barrier():
         if pg is not None:
@@ -258,7 +260,7 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "phase-point updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweep / f64 moments", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": prob.ncell, "velocities": prob.nvel,
+        "config": {"workload": workload, "cells": prob.ncell, "velocities": prob.nvel,
                    "phase_points_per_step": pp, "precision": "mixed", "v_per_cta": info["v_per_cta"],
                    "block_z": info["block_z"], "sweep_stages": info["n_stages"],
                    "device_bytes": info["device_bytes"],
@@ -281,6 +283,8 @@ def main():
     ap.add_argument("--block-z", type=int, default=0)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=N_CELL, help="cells per side (profiling runs only)")
+    ap.add_argument("--vels", type=int, default=N_VEL, help="velocities per side (profiling runs only)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":

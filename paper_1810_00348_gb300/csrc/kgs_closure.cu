@@ -88,13 +88,23 @@ __global__ void __launch_bounds__(RED_THREADS) close_kernel(const CloseArgs a)
         double F[6] = {0, 0, 0, 0, 0, 0};
         for (int q = 0; q < 13; q++) S[q] = 0.0;
         for (int g = 0; g < a.n_vg; g++) {
-            const double *pp = a.part + (size_t)g * NPART * ncell + c;
-            for (int q = 0; q < 13; q++) S[q] += pp[(size_t)q * ncell];
+            double v[NPART];
+            if (sizeof(Real) == 8) {
+                const double *pp = static_cast<const double *>(a.part) + (size_t)g * NPART * ncell + c;
+                for (int q = 0; q < NPART; q++) v[q] = pp[(size_t)q * ncell];
+            } else {
+                const float2 *pp = static_cast<const float2 *>(a.part) + (size_t)g * NPART * ncell + c;
+                for (int q = 0; q < NPART; q++) {
+                    const float2 e = pp[(size_t)q * ncell];
+                    v[q] = (double)e.x - (double)e.y;
+                }
+            }
+            for (int q = 0; q < 13; q++) S[q] += v[q];
             const int o = a.vg_oct[g];
             // incoming flux onto the wall ahead of the octant along each axis
-            F[(o & 1) ? 1 : 0] += pp[(size_t)P_FX * ncell];
-            F[(o & 2) ? 3 : 2] += pp[(size_t)P_FY * ncell];
-            F[(o & 4) ? 5 : 4] += pp[(size_t)P_FZ * ncell];
+            F[(o & 1) ? 1 : 0] += v[P_FX];
+            F[(o & 2) ? 3 : 2] += v[P_FY];
+            F[(o & 4) ? 5 : 4] += v[P_FZ];
         }
         const Real *cf = static_cast<const Real *>(a.coef) + c * NCOEF;
         // The sums were taken about the lagged velocity U^n as stored in the

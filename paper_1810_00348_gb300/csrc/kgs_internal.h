@@ -25,10 +25,10 @@ enum {
     C_KAPPA,                // (1/tau) rho (2 pi R T)^{-3/2}
     C_NEXP,                 // exponent scale: -1/(2RT) (FP64) or -log2(e)/(2RT) (FP32)
     C_RT1,                  // 1/(R T)
-    C_QX, C_QY, C_QZ,       // (1 - Pr) q / (5 p R T)
     C_RTAU,                 // 1/tau
-    C_RDX, C_RDY, C_RDZ,    // 1/dx_i, 1/dy_j, 1/dz_k
     C_FLAGS,                // cell flags (below), stored as a small integer value
+    C_QX, C_QY, C_QZ,       // (1 - Pr) q / (5 p R T)
+    C_RDX, C_RDY, C_RDZ,    // 1/dx_i, 1/dy_j, 1/dz_k
     C_PAD0, C_PAD1
 };
 
@@ -60,27 +60,32 @@ struct SweepArgs {
     int Nv;                       // all velocities
     int vg_size;                  // velocities per CTA
     const void *vel;              // Real[Nv][4]: xi_x, xi_y, xi_z, w (octant-sorted)
-    const void *velw;             // Real[Nv][2]: w_x, w_y * w_z (tensor-product factors of w)
+    const void *velm;             // Real[Nv][8]: w_x, w_y w_z, and the low parts of xi_x, xi_y,
+                                  // xi_z (xi = hi + lo with hi = the value in vel), 3 unused
     int oct_nx[8];                // x nodes in each octant (length of its velocity x-lines)
+    int nxo_max;                  // max over octants of oct_nx
+    int any_solid;                // the problem has solid cells
     const void *coef;             // Real[ncell][NCOEF]
     const double *rho_w;          // [6][ncell]
     const void *mtab;             // Real[MT_ROWS][Nv]: unit wall Maxwellians, free stream
     int side_inflow[6];           // domain side s is a free-stream boundary
     void *FX, *FY, *FZ;           // face planes: [nz*ny][Nv], [nz*nx][Nv], [ny*nx][Nv]
-    double *part;                 // [n_vg][NPART][ncell]
+    void *part;                   // [n_vg][NPART][ncell]: double (FP64 path) or float2 (s, c)
+                                  // with value s - c (FP32 path, Kahan pair)
     unsigned long long ncell;
+    int line16;                   // every octant has x-lines of 16 nodes (specialised moment loop)
 };
 
 // Sweep launch (one wavefront stage).  precision: 0 FP64, 1 FP32.
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s);
-size_t sweep_smem_bytes(int precision, int tv);
+size_t sweep_smem_bytes(int precision, int tv, int nxo_max);
 
 struct CloseArgs {
     int nx, ny, nz;
     unsigned long long ncell;
     int n_vg;
     const int *vg_oct;            // [n_vg] octant of each velocity group
-    const double *part;           // [n_vg][NPART][ncell]
+    const void *part;             // [n_vg][NPART][ncell], see SweepArgs::part
     const void *coef;             // sweep-precision coefficients (U centre)
     int precision;
     const double *mac;            // [8][ncell] step n

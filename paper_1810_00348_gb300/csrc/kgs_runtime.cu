@@ -13,58 +13,35 @@
 
 #include <algorithm>
 #include <cmath>
-#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "../../include/kgs.h"
-#include "kgs_internal.h"
+#include "kgs_tables.h"
 
 using namespace kgs;
 
 namespace {
-
-constexpr double R_GAS = 0.5;
 constexpr uint32_t CKPT_MAGIC = 0x4b475331u;  // "KGS1"
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-}  // namespace
+}
 
 struct kgs_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;
-    int nx = 0, ny = 0, nz = 0, nvx = 0, nvy = 0, nvz = 0;
-    size_t ncell = 0;
-    int Nv = 0;
-    long long n_fluid = 0;
-    int precision = KGS_FP64;
-    int wall_norm_mode = KGS_WALL_DISCRETE;
+    HostTables t;
     int mass_rescale = 0;
     int max_iters = 1000;
     double tol = 1e-8;
-    int tv = 1, vg_size = NT, bz = 16;
-    double mu_ref = 0.0, omega = 0.81, Pr = 2.0 / 3.0;
     double M0 = 0.0;
     int iteration = 0;
     double last_residual = -1.0;
-    int nbx = 0, nby = 0, nbz = 0;
-    int oct_vstart[8] = {0}, oct_vcount[8] = {0}, oct_vgbase[8] = {0}, oct_nx[8] = {0};
-    int n_vg = 0, max_vg = 0;
-    int side_inflow[6] = {0};
-    bool any_inflow = false;
-    kgs_bc bc{};
-    std::vector<int> stage_off, stage_n;
-    std::vector<double> dx, dy, dz;
-    std::vector<uint8_t> solid_h;
+    int n_red_blocks = 0;
     // device buffers
     double *mac = nullptr, *mac_new = nullptr, *rho_w = nullptr, *rho_w_new = nullptr;
-    void *coef = nullptr, *vel = nullptr, *velw = nullptr, *mtab = nullptr, *FX = nullptr, *FY = nullptr, *FZ = nullptr;
-    double *vel64 = nullptr, *part = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;
+    void *coef = nullptr, *vel = nullptr, *velm = nullptr, *mtab = nullptr, *FX = nullptr, *FY = nullptr,
+         *FZ = nullptr;
+    void *part = nullptr;
+    double *vel64 = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;
     double *ddx = nullptr, *ddy = nullptr, *ddz = nullptr;
     uint8_t *solid = nullptr, *side_flags = nullptr;
     int8_t *wall_kind = nullptr;
@@ -74,7 +51,6 @@ struct kgs_ctx {
     double *blk_mass = nullptr, *blk_res = nullptr, *scale = nullptr, *resid = nullptr;
     int *blk_bad = nullptr;
     double *h_resid = nullptr;  // pinned
-    int n_red_blocks = 0;
     size_t device_bytes = 0;
     std::vector<void *> allocs;
     // profiling
@@ -93,9 +69,9 @@ int cuda_err(cudaError_t e)
     return KGS_ECUDA;
 }
 
-#define KGS_CHECK(call)                      \
-    do {                                     \
-        cudaError_t e_ = (call);             \
+#define KGS_CHECK(call)                             \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
         if (e_ != cudaSuccess) return cuda_err(e_); \
     } while (0)
 
@@ -128,11 +104,15 @@ int upload(kgs_ctx *c, T **p, const std::vector<T> &h)
     return cuda_err(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
 }
 
-double maxwellian(double rho, const double U[3], double T, const double xi[3])
+// Upload a FP64 host table into a device buffer of the sweep precision.
+int upload_real(kgs_ctx *c, void **p, const std::vector<double> &h)
 {
-    double c2 = 0.0;
-    for (int d = 0; d < 3; d++) c2 += (xi[d] - U[d]) * (xi[d] - U[d]);
-    return rho / std::pow(2.0 * M_PI * R_GAS * T, 1.5) * std::exp(-c2 / (2.0 * R_GAS * T));
+    const size_t rsz = c->t.real_bytes();
+    int rc = dalloc(c, p, h.size() * rsz);
+    if (rc) return rc;
+    if (rsz == sizeof(double)) return cuda_err(cudaMemcpy(*p, h.data(), h.size() * rsz, cudaMemcpyHostToDevice));
+    std::vector<float> f(h.begin(), h.end());
+    return cuda_err(cudaMemcpy(*p, f.data(), f.size() * rsz, cudaMemcpyHostToDevice));
 }
 
 void free_all(kgs_ctx *c)
@@ -147,37 +127,38 @@ void free_all(kgs_ctx *c)
 
 // Upload macros (or the uniform state), set M0 and the wall densities from
 // the flux of the initial equilibrium.
-int initial_state(kgs_ctx *c, const double *macros, const kgs_bc *bc_uniform)
+int initial_state(kgs_ctx *c, const double *macros)
 {
-    const size_t n = c->ncell;
+    const HostTables &t = c->t;
+    const size_t n = t.ncell;
     std::vector<double> m(8 * n);
     if (macros) {
         std::memcpy(m.data(), macros, sizeof(double) * 8 * n);
     } else {
         double u[8] = {1.0, 0, 0, 0, 1.0, 0, 0, 0};
-        if (bc_uniform) {
-            u[0] = bc_uniform->rho_in;
-            u[1] = bc_uniform->U_in[0];
-            u[2] = bc_uniform->U_in[1];
-            u[3] = bc_uniform->U_in[2];
-            u[4] = bc_uniform->T_in;
+        if (t.any_inflow) {
+            u[0] = t.bc.rho_in;
+            u[1] = t.bc.U_in[0];
+            u[2] = t.bc.U_in[1];
+            u[3] = t.bc.U_in[2];
+            u[4] = t.bc.T_in;
         }
         for (int q = 0; q < 8; q++)
             for (size_t i = 0; i < n; i++) m[q * n + i] = u[q];
     }
     double M0 = 0.0;
     for (size_t i = 0; i < n; i++) {
-        if (!c->solid_h.empty() && c->solid_h[i]) {
+        if (t.any_solid && t.solid[i]) {
             for (int q = 0; q < 8; q++) m[q * n + i] = 0.0;
             continue;
         }
         if (!(m[i] > 0.0) || !(m[4 * n + i] > 0.0)) return KGS_EINVAL;
-        const size_t ii = i % c->nx, jj = (i / c->nx) % c->ny, kk = i / ((size_t)c->nx * c->ny);
-        M0 += m[i] * c->dx[ii] * c->dy[jj] * c->dz[kk];
+        const size_t ii = i % t.nx, jj = (i / t.nx) % t.ny, kk = i / ((size_t)t.nx * t.ny);
+        M0 += m[i] * t.dx[ii] * t.dy[jj] * t.dz[kk];
     }
     c->M0 = M0;
     KGS_CHECK(cudaMemcpyAsync(c->mac, m.data(), sizeof(double) * 8 * n, cudaMemcpyHostToDevice, c->stream));
-    KGS_CHECK(launch_wall_flux_init(c->mac, c->wall_kind, c->wall_norm, c->vel64, c->Nv, n, R_GAS, c->Pr, c->rho_w,
+    KGS_CHECK(launch_wall_flux_init(c->mac, c->wall_kind, c->wall_norm, c->vel64, t.Nv, n, R_GAS, t.Pr, c->rho_w,
                                     c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     c->iteration = 0;
@@ -185,53 +166,67 @@ int initial_state(kgs_ctx *c, const double *macros, const kgs_bc *bc_uniform)
     return KGS_OK;
 }
 
-int run_iteration(kgs_ctx *c, double *residual, int *bad)
+SweepArgs sweep_args(const kgs_ctx *c)
 {
-    cudaStream_t st = c->stream;
-    KGS_CHECK(launch_coef(c->precision, c->mac, c->solid, c->side_flags, c->rdx, c->rdy, c->rdz, c->nx, c->ny, c->nz,
-                          c->mu_ref, c->omega, c->Pr, c->coef, st));
+    const HostTables &t = c->t;
     SweepArgs a;
-    a.nx = c->nx;
-    a.ny = c->ny;
-    a.nz = c->nz;
-    a.bz = c->bz;
-    a.nbx = c->nbx;
-    a.nby = c->nby;
-    a.nbz = c->nbz;
+    a.nx = t.nx;
+    a.ny = t.ny;
+    a.nz = t.nz;
+    a.bz = t.bz;
+    a.nbx = t.nbx;
+    a.nby = t.nby;
+    a.nbz = t.nbz;
+    a.work = c->work;
     a.oct_vstart = c->d_vstart;
     a.oct_vcount = c->d_vcount;
     a.oct_vgbase = c->d_vgbase;
-    a.Nv = c->Nv;
-    a.vg_size = c->vg_size;
+    a.Nv = t.Nv;
+    a.vg_size = t.vg_size;
     a.vel = c->vel;
-    a.velw = c->velw;
-    for (int o = 0; o < 8; o++) a.oct_nx[o] = c->oct_nx[o] > 0 ? c->oct_nx[o] : 1;
+    a.velm = c->velm;
+    a.nxo_max = t.nxo_max;
+    for (int o = 0; o < 8; o++) a.oct_nx[o] = t.oct_nx[o] > 0 ? t.oct_nx[o] : 1;
+    a.any_solid = t.any_solid ? 1 : 0;
     a.coef = c->coef;
     a.rho_w = c->rho_w;
     a.mtab = c->mtab;
-    for (int s = 0; s < 6; s++) a.side_inflow[s] = c->side_inflow[s];
+    for (int s = 0; s < 6; s++) a.side_inflow[s] = t.side_inflow[s];
     a.FX = c->FX;
     a.FY = c->FY;
     a.FZ = c->FZ;
     a.part = c->part;
-    a.ncell = c->ncell;
-    const int ns = (int)c->stage_n.size();
+    a.ncell = t.ncell;
+    a.line16 = 1;
+    for (int o = 0; o < 8; o++)
+        if (t.oct_vcount[o] > 0 && t.oct_nx[o] != 16) a.line16 = 0;
+    return a;
+}
+
+int run_iteration(kgs_ctx *c, double *residual, int *bad)
+{
+    const HostTables &t = c->t;
+    cudaStream_t st = c->stream;
+    KGS_CHECK(launch_coef(t.precision, c->mac, c->solid, c->side_flags, c->rdx, c->rdy, c->rdz, t.nx, t.ny, t.nz,
+                          t.mu_ref, t.omega, t.Pr, c->coef, st));
+    SweepArgs a = sweep_args(c);
+    const int ns = (int)t.stage_n.size();
     for (int s = 0; s < ns; s++) {
-        a.work = c->work + c->stage_off[s];
+        a.work = c->work + t.stage_off[s];
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[2 * s], st));
-        KGS_CHECK(launch_sweep(c->precision, c->tv, a, c->stage_n[s], c->max_vg, st));
+        KGS_CHECK(launch_sweep(t.precision, t.tv, a, t.stage_n[s], t.max_vg, st));
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[2 * s + 1], st));
     }
     CloseArgs ca;
-    ca.nx = c->nx;
-    ca.ny = c->ny;
-    ca.nz = c->nz;
-    ca.ncell = c->ncell;
-    ca.n_vg = c->n_vg;
+    ca.nx = t.nx;
+    ca.ny = t.ny;
+    ca.nz = t.nz;
+    ca.ncell = t.ncell;
+    ca.n_vg = t.n_vg;
     ca.vg_oct = c->d_vg_oct;
     ca.part = c->part;
     ca.coef = c->coef;
-    ca.precision = c->precision;
+    ca.precision = t.precision;
     ca.mac = c->mac;
     ca.mac_new = c->mac_new;
     ca.rho_w_new = c->rho_w_new;
@@ -244,7 +239,7 @@ int run_iteration(kgs_ctx *c, double *residual, int *bad)
     ca.blk_mass = c->blk_mass;
     KGS_CHECK(launch_close(ca, c->n_red_blocks, st));
     KGS_CHECK(launch_finalize_mass(c->blk_mass, c->n_red_blocks, c->M0, c->mass_rescale, c->scale, st));
-    KGS_CHECK(launch_scale_residual(c->mac_new, c->rho_w_new, c->mac, c->solid, c->ncell, c->scale, c->blk_res,
+    KGS_CHECK(launch_scale_residual(c->mac_new, c->rho_w_new, c->mac, c->solid, t.ncell, c->scale, c->blk_res,
                                     c->blk_bad, c->n_red_blocks, st));
     KGS_CHECK(launch_finalize_residual(c->blk_res, c->blk_bad, c->n_red_blocks, c->resid, st));
     KGS_CHECK(cudaMemcpyAsync(c->h_resid, c->resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -289,265 +284,64 @@ const char *kgs_strerror(int code)
 int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
               const kgs_bc *bc, const kgs_opts *opts)
 {
-    if (!out || !grid || !vg || !gas || !bc || !opts) return KGS_EINVAL;
+    if (!out || !opts) return KGS_EINVAL;
     *out = nullptr;
-    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !grid->dx || !grid->dy || !grid->dz) return KGS_EINVAL;
-    if (vg->nvx < 1 || vg->nvy < 1 || vg->nvz < 1) return KGS_EINVAL;
-    if (!vg->xi_x || !vg->xi_y || !vg->xi_z || !vg->w_x || !vg->w_y || !vg->w_z) return KGS_EINVAL;
-    if (!(gas->Kn > 0.0) || !(gas->Pr > 0.0) || !(gas->omega >= 0.0 && gas->omega <= 1.5)) return KGS_EINVAL;
-    if (opts->precision != KGS_FP64 && opts->precision != KGS_MIXED) return KGS_EINVAL;
-    if (opts->wall_norm != KGS_WALL_DISCRETE && opts->wall_norm != KGS_WALL_ANALYTIC) return KGS_EINVAL;
-    if (opts->v_per_cta != 0 && opts->v_per_cta != 128 && opts->v_per_cta != 256) return KGS_EINVAL;
-    if (opts->precision == KGS_FP64 && opts->v_per_cta == 256) return KGS_EINVAL;
-    if (opts->block_z < 0) return KGS_EINVAL;
-    const long long ncell_ll = (long long)grid->nx * grid->ny * grid->nz;
-    const long long nv_ll = (long long)vg->nvx * vg->nvy * vg->nvz;
-    if (ncell_ll > (1LL << 31) || nv_ll > (1LL << 24)) return KGS_EINVAL;
-    for (int i = 0; i < grid->nx; i++) if (!(grid->dx[i] > 0.0)) return KGS_EINVAL;
-    for (int i = 0; i < grid->ny; i++) if (!(grid->dy[i] > 0.0)) return KGS_EINVAL;
-    for (int i = 0; i < grid->nz; i++) if (!(grid->dz[i] > 0.0)) return KGS_EINVAL;
-    for (int i = 0; i < vg->nvx; i++) if (!(vg->w_x[i] > 0.0) || !std::isfinite(vg->xi_x[i])) return KGS_EINVAL;
-    for (int i = 0; i < vg->nvy; i++) if (!(vg->w_y[i] > 0.0) || !std::isfinite(vg->xi_y[i])) return KGS_EINVAL;
-    for (int i = 0; i < vg->nvz; i++) if (!(vg->w_z[i] > 0.0) || !std::isfinite(vg->xi_z[i])) return KGS_EINVAL;
-    bool any_inflow = false, any_solid = false;
-    for (int s = 0; s < 6; s++) {
-        if (bc->type[s] != KGS_FACE_WALL && bc->type[s] != KGS_FACE_INFLOW) return KGS_EINVAL;
-        if (bc->type[s] == KGS_FACE_WALL && !(bc->T_w[s] > 0.0)) return KGS_EINVAL;
-        any_inflow |= bc->type[s] == KGS_FACE_INFLOW;
-    }
-    if (any_inflow && (!(bc->rho_in > 0.0) || !(bc->T_in > 0.0))) return KGS_EINVAL;
-    if (solid)
-        for (long long i = 0; i < ncell_ll; i++) any_solid |= solid[i] != 0;
-    if (any_solid && !(bc->T_solid > 0.0)) return KGS_EINVAL;
-    if (std::isinf(gas->Kn)) {
-        // free-molecular limit: a velocity with all components zero has no
-        // equation (0 = 0); reject such grids
-        bool zx = false, zy = false, zz = false;
-        for (int i = 0; i < vg->nvx; i++) zx |= vg->xi_x[i] == 0.0;
-        for (int i = 0; i < vg->nvy; i++) zy |= vg->xi_y[i] == 0.0;
-        for (int i = 0; i < vg->nvz; i++) zz |= vg->xi_z[i] == 0.0;
-        if (zx && zy && zz) return KGS_EINVAL;
-    }
-
+    int rc = validate_problem(grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta,
+                              opts->block_z);
+    if (rc) return rc;
     kgs_ctx *c = new (std::nothrow) kgs_ctx();
     if (!c) return KGS_ENOMEM;
-    auto fail = [&](int rc) {
+    auto fail = [&](int code) {
         free_all(c);
         delete c;
-        return rc;
+        return code;
     };
     if (cudaGetDevice(&c->dev) != cudaSuccess) return fail(KGS_ECUDA);
     c->stream = static_cast<cudaStream_t>(opts->stream);
-    c->nx = grid->nx;
-    c->ny = grid->ny;
-    c->nz = grid->nz;
-    c->ncell = (size_t)ncell_ll;
-    c->nvx = vg->nvx;
-    c->nvy = vg->nvy;
-    c->nvz = vg->nvz;
-    c->Nv = (int)nv_ll;
-    c->precision = opts->precision;
-    c->wall_norm_mode = opts->wall_norm;
     c->mass_rescale = opts->mass_rescale ? 1 : 0;
     c->max_iters = opts->max_iters > 0 ? opts->max_iters : 1000;
     c->tol = opts->tol > 0.0 ? opts->tol : 1e-8;
-    c->tv = (opts->precision == KGS_FP64) ? 1 : (opts->v_per_cta == 256 ? 2 : 1);
-    c->vg_size = NT * c->tv;
-    c->bz = opts->block_z > 0 ? opts->block_z : 16;
-    c->omega = gas->omega;
-    c->Pr = gas->Pr;
-    // Eq. (10) with T_ref = 1, p_ref = rho_ref R T_ref = 1/2, lambda_ref = Kn
-    c->mu_ref = 15.0 * std::sqrt(M_PI) * (R_GAS * 1.0) * gas->Kn /
-                ((5.0 - 2.0 * gas->omega) * (7.0 - 2.0 * gas->omega) * std::sqrt(2.0 * R_GAS * 1.0));
-    c->dx.assign(grid->dx, grid->dx + c->nx);
-    c->dy.assign(grid->dy, grid->dy + c->ny);
-    c->dz.assign(grid->dz, grid->dz + c->nz);
-    if (any_solid) c->solid_h.assign(solid, solid + c->ncell);
-    for (int s = 0; s < 6; s++) c->side_inflow[s] = bc->type[s] == KGS_FACE_INFLOW;
-    c->any_inflow = any_inflow;
-    c->bc = *bc;
-    const size_t n = c->ncell;
-    const int nx = c->nx, ny = c->ny, nz = c->nz;
-
-    // ---- velocities sorted by octant (bit d set: xi_d >= 0), ix fastest ----
-    std::vector<int> order;
-    order.reserve(c->Nv);
-    auto oct_of = [&](int ix, int iy, int iz) {
-        return (vg->xi_x[ix] >= 0.0 ? 1 : 0) | (vg->xi_y[iy] >= 0.0 ? 2 : 0) | (vg->xi_z[iz] >= 0.0 ? 4 : 0);
-    };
-    for (int o = 0; o < 8; o++) {
-        c->oct_vstart[o] = (int)order.size();
-        for (int iz = 0; iz < c->nvz; iz++)
-            for (int iy = 0; iy < c->nvy; iy++)
-                for (int ix = 0; ix < c->nvx; ix++)
-                    if (oct_of(ix, iy, iz) == o) order.push_back(ix + c->nvx * (iy + c->nvy * iz));
-        c->oct_vcount[o] = (int)order.size() - c->oct_vstart[o];
-    }
-    for (int o = 0; o < 8; o++) {
-        int cnt = 0;
-        for (int ix = 0; ix < c->nvx; ix++) cnt += ((vg->xi_x[ix] >= 0.0 ? 1 : 0) == (o & 1));
-        c->oct_nx[o] = cnt;
-    }
-    std::vector<double> vel64((size_t)c->Nv * 4), velw64((size_t)c->Nv * 2);
-    for (int g = 0; g < c->Nv; g++) {
-        const int a = order[g];
-        const int ix = a % c->nvx, iy = (a / c->nvx) % c->nvy, iz = a / (c->nvx * c->nvy);
-        vel64[g * 4 + 0] = vg->xi_x[ix];
-        vel64[g * 4 + 1] = vg->xi_y[iy];
-        vel64[g * 4 + 2] = vg->xi_z[iz];
-        vel64[g * 4 + 3] = vg->w_x[ix] * vg->w_y[iy] * vg->w_z[iz];
-        velw64[g * 2 + 0] = vg->w_x[ix];
-        velw64[g * 2 + 1] = vg->w_y[iy] * vg->w_z[iz];
-    }
-    std::vector<int> vg_oct;
-    for (int o = 0; o < 8; o++) {
-        c->oct_vgbase[o] = (int)vg_oct.size();
-        const int ng = (c->oct_vcount[o] + c->vg_size - 1) / c->vg_size;
-        for (int g = 0; g < ng; g++) vg_oct.push_back(o);
-        c->max_vg = std::max(c->max_vg, ng);
-    }
-    c->n_vg = (int)vg_oct.size();
-
-    // ---- wall tables ----
-    double wallU[7][3], wallT[7];
-    for (int s = 0; s < 6; s++) {
-        for (int d = 0; d < 3; d++) wallU[s][d] = bc->U_w[s][d];
-        wallT[s] = bc->type[s] == KGS_FACE_WALL ? bc->T_w[s] : 1.0;
-    }
-    wallU[6][0] = wallU[6][1] = wallU[6][2] = 0.0;
-    wallT[6] = any_solid ? bc->T_solid : 1.0;
-    std::vector<double> wall_norm(7 * 6);
-    for (int k = 0; k < 7; k++)
-        for (int s = 0; s < 6; s++) {
-            if (c->wall_norm_mode == KGS_WALL_ANALYTIC) {
-                wall_norm[k * 6 + s] = std::sqrt(2.0 * M_PI / (R_GAS * wallT[k]));
-                continue;
-            }
-            // discrete outgoing flux of the unit wall Maxwellian
-            const int d = s / 2;
-            const double nrm = (s % 2) ? -1.0 : 1.0;
-            double D = 0.0;
-            for (int g = 0; g < c->Nv; g++) {
-                const double *v = &vel64[g * 4];
-                const double xn = v[d] * nrm;
-                if (xn > 0.0) D += v[3] * xn * maxwellian(1.0, wallU[k], wallT[k], v);
-            }
-            wall_norm[k * 6 + s] = D > 0.0 ? 1.0 / D : 0.0;
-        }
-    std::vector<double> mt((size_t)MT_ROWS * c->Nv);
-    for (int g = 0; g < c->Nv; g++) {
-        const double *v = &vel64[g * 4];
-        for (int k = 0; k < 7; k++) mt[(size_t)k * c->Nv + g] = maxwellian(1.0, wallU[k], wallT[k], v);
-        mt[(size_t)MT_INFLOW * c->Nv + g] = any_inflow ? maxwellian(bc->rho_in, bc->U_in, bc->T_in, v) : 0.0;
-    }
-    // per (side, cell): wall kind and flags
-    std::vector<int8_t> wall_kind(6 * n, -1);
-    std::vector<uint8_t> side_flags(2 * n, 0);
-    long long n_fluid = 0;
-    for (int k = 0; k < nz; k++)
-        for (int j = 0; j < ny; j++)
-            for (int i = 0; i < nx; i++) {
-                const size_t cidx = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
-                if (any_solid && solid[cidx]) continue;
-                n_fluid++;
-                for (int s = 0; s < 6; s++) {
-                    int ii = i, jj = j, kk = k;
-                    const int step = (s % 2) ? 1 : -1;
-                    if (s / 2 == 0) ii += step;
-                    if (s / 2 == 1) jj += step;
-                    if (s / 2 == 2) kk += step;
-                    const bool outside = ii < 0 || jj < 0 || kk < 0 || ii >= nx || jj >= ny || kk >= nz;
-                    if (outside) {
-                        if (bc->type[s] == KGS_FACE_WALL) {
-                            wall_kind[s * n + cidx] = (int8_t)s;
-                            side_flags[n + cidx] |= (uint8_t)(1 << s);
-                        }
-                    } else {
-                        const size_t nb = (size_t)ii + (size_t)nx * ((size_t)jj + (size_t)ny * kk);
-                        if (any_solid && solid[nb]) {
-                            wall_kind[s * n + cidx] = 6;
-                            side_flags[cidx] |= (uint8_t)(1 << s);
-                            side_flags[n + cidx] |= (uint8_t)(1 << s);
-                        }
-                    }
-                }
-            }
-    c->n_fluid = n_fluid;
-
-    // ---- wavefront stages over blocks ----
-    c->nbx = (nx + BX - 1) / BX;
-    c->nby = (ny + BY - 1) / BY;
-    c->nbz = (nz + c->bz - 1) / c->bz;
-    const int n_stages = c->nbx + c->nby + c->nbz - 2;
-    std::vector<std::vector<int4>> stages(n_stages);
-    for (int o = 0; o < 8; o++) {
-        if (c->oct_vcount[o] == 0) continue;
-        for (int bzr = 0; bzr < c->nbz; bzr++)
-            for (int byr = 0; byr < c->nby; byr++)
-                for (int bxr = 0; bxr < c->nbx; bxr++) stages[bxr + byr + bzr].push_back(make_int4(o, bxr, byr, bzr));
-    }
-    std::vector<int4> work;
-    for (int s = 0; s < n_stages; s++) {
-        c->stage_off.push_back((int)work.size());
-        c->stage_n.push_back((int)stages[s].size());
-        work.insert(work.end(), stages[s].begin(), stages[s].end());
-    }
-
-    // ---- device allocations ----
-    int rc = KGS_OK;
-    const size_t rsz = c->precision == KGS_FP64 ? sizeof(double) : sizeof(float);
-    std::vector<double> rdx(nx), rdy(ny), rdz(nz);
-    for (int i = 0; i < nx; i++) rdx[i] = 1.0 / c->dx[i];
-    for (int i = 0; i < ny; i++) rdy[i] = 1.0 / c->dy[i];
-    for (int i = 0; i < nz; i++) rdz[i] = 1.0 / c->dz[i];
+    HostTables &t = c->t;
+    build_tables(t, grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta, opts->block_z);
+    const size_t n = t.ncell;
+    const size_t rsz = t.real_bytes();
     c->n_red_blocks = (int)((n + 255) / 256);
     if ((rc = dalloc_t(c, &c->mac, 8 * n)) || (rc = dalloc_t(c, &c->mac_new, 8 * n)) ||
         (rc = dalloc_t(c, &c->rho_w, 6 * n)) || (rc = dalloc_t(c, &c->rho_w_new, 6 * n)) ||
-        (rc = dalloc(c, &c->coef, n * NCOEF * rsz)) || (rc = upload(c, &c->vel64, vel64)) ||
-        (rc = dalloc(c, &c->vel, (size_t)c->Nv * 4 * rsz)) || (rc = dalloc(c, &c->velw, (size_t)c->Nv * 2 * rsz)) || (rc = dalloc(c, &c->mtab, mt.size() * rsz)) ||
-        (rc = dalloc(c, &c->FX, (size_t)nz * ny * c->Nv * rsz)) ||
-        (rc = dalloc(c, &c->FY, (size_t)nz * nx * c->Nv * rsz)) ||
-        (rc = dalloc(c, &c->FZ, (size_t)ny * nx * c->Nv * rsz)) ||
-        (rc = dalloc_t(c, &c->part, (size_t)c->n_vg * NPART * n)) || (rc = upload(c, &c->rdx, rdx)) ||
-        (rc = upload(c, &c->rdy, rdy)) || (rc = upload(c, &c->rdz, rdz)) || (rc = upload(c, &c->ddx, c->dx)) ||
-        (rc = upload(c, &c->ddy, c->dy)) || (rc = upload(c, &c->ddz, c->dz)) ||
-        (rc = upload(c, &c->side_flags, side_flags)) || (rc = upload(c, &c->wall_kind, wall_kind)) ||
-        (rc = upload(c, &c->wall_norm, wall_norm)) || (rc = upload(c, &c->work, work)) ||
-        (rc = upload(c, &c->d_vstart, std::vector<int>(c->oct_vstart, c->oct_vstart + 8))) ||
-        (rc = upload(c, &c->d_vcount, std::vector<int>(c->oct_vcount, c->oct_vcount + 8))) ||
-        (rc = upload(c, &c->d_vgbase, std::vector<int>(c->oct_vgbase, c->oct_vgbase + 8))) ||
-        (rc = upload(c, &c->d_vg_oct, vg_oct)) || (rc = dalloc_t(c, &c->blk_mass, c->n_red_blocks)) ||
+        (rc = dalloc(c, &c->coef, n * NCOEF * rsz)) || (rc = upload(c, &c->vel64, t.vel64)) ||
+        (rc = upload_real(c, &c->vel, t.vel64)) || (rc = upload_real(c, &c->mtab, t.mt)) ||
+        (rc = dalloc(c, &c->FX, (size_t)t.nz * t.ny * t.Nv * rsz)) ||
+        (rc = dalloc(c, &c->FY, (size_t)t.nz * t.nx * t.Nv * rsz)) ||
+        (rc = dalloc(c, &c->FZ, (size_t)t.ny * t.nx * t.Nv * rsz)) ||
+        (rc = dalloc(c, &c->part, (size_t)t.n_vg * NPART * n * 8)) || (rc = upload(c, &c->rdx, t.rdx)) ||
+        (rc = upload(c, &c->rdy, t.rdy)) || (rc = upload(c, &c->rdz, t.rdz)) || (rc = upload(c, &c->ddx, t.dx)) ||
+        (rc = upload(c, &c->ddy, t.dy)) || (rc = upload(c, &c->ddz, t.dz)) ||
+        (rc = upload(c, &c->side_flags, t.side_flags)) || (rc = upload(c, &c->wall_kind, t.wall_kind)) ||
+        (rc = upload(c, &c->wall_norm, t.wall_norm)) || (rc = upload(c, &c->work, t.work)) ||
+        (rc = upload(c, &c->d_vstart, std::vector<int>(t.oct_vstart, t.oct_vstart + 8))) ||
+        (rc = upload(c, &c->d_vcount, std::vector<int>(t.oct_vcount, t.oct_vcount + 8))) ||
+        (rc = upload(c, &c->d_vgbase, std::vector<int>(t.oct_vgbase, t.oct_vgbase + 8))) ||
+        (rc = upload(c, &c->d_vg_oct, t.vg_oct)) || (rc = dalloc_t(c, &c->blk_mass, c->n_red_blocks)) ||
         (rc = dalloc_t(c, &c->blk_res, (size_t)c->n_red_blocks * 10)) ||
         (rc = dalloc_t(c, &c->blk_bad, c->n_red_blocks)) || (rc = dalloc_t(c, &c->scale, 2)) ||
         (rc = dalloc_t(c, &c->resid, 2)))
         return fail(rc);
-    if (any_solid) {
-        if ((rc = upload(c, &c->solid, c->solid_h))) return fail(rc);
-    }
-    if (c->precision == KGS_FP64) {
-        if (cudaMemcpy(c->vel, vel64.data(), vel64.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->velw, velw64.data(), velw64.size() * sizeof(double), cudaMemcpyHostToDevice) !=
-                cudaSuccess ||
-            cudaMemcpy(c->mtab, mt.data(), mt.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(KGS_ECUDA);
+    if (t.precision == KGS_FP64) {
+        if ((rc = upload(c, reinterpret_cast<double **>(&c->velm), t.velm64))) return fail(rc);
     } else {
-        std::vector<float> v32(vel64.begin(), vel64.end()), m32(mt.begin(), mt.end());
-        std::vector<float> w32(velw64.begin(), velw64.end());
-        if (cudaMemcpy(c->vel, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->velw, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(c->mtab, m32.data(), m32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail(KGS_ECUDA);
+        if ((rc = upload(c, reinterpret_cast<float **>(&c->velm), t.velm32))) return fail(rc);
     }
-    if (cudaMemset(c->FX, 0, (size_t)nz * ny * c->Nv * rsz) != cudaSuccess ||
-        cudaMemset(c->FY, 0, (size_t)nz * nx * c->Nv * rsz) != cudaSuccess ||
-        cudaMemset(c->FZ, 0, (size_t)ny * nx * c->Nv * rsz) != cudaSuccess ||
+    if (t.any_solid && (rc = upload(c, &c->solid, t.solid))) return fail(rc);
+    if (cudaMemset(c->FX, 0, (size_t)t.nz * t.ny * t.Nv * rsz) != cudaSuccess ||
+        cudaMemset(c->FY, 0, (size_t)t.nz * t.nx * t.Nv * rsz) != cudaSuccess ||
+        cudaMemset(c->FZ, 0, (size_t)t.ny * t.nx * t.Nv * rsz) != cudaSuccess ||
         cudaMemset(c->coef, 0, n * NCOEF * rsz) != cudaSuccess)
         return fail(KGS_ECUDA);
     if (cudaMallocHost(&c->h_resid, 2 * sizeof(double)) != cudaSuccess) return fail(KGS_ENOMEM);
-    c->ev.resize(2 * (size_t)n_stages);
+    c->ev.resize(2 * t.stage_n.size());
     for (auto &e : c->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(KGS_ECUDA);
-    if ((rc = initial_state(c, nullptr, any_inflow ? bc : nullptr))) return fail(rc);
+    if ((rc = initial_state(c, nullptr))) return fail(rc);
     *out = c;
     return KGS_OK;
 }
@@ -556,7 +350,7 @@ int kgs_set_initial(kgs_ctx *c, const double *macros)
 {
     if (!c) return KGS_EINVAL;
     if (cudaSetDevice(c->dev) != cudaSuccess) return KGS_ECUDA;
-    return initial_state(c, macros, c->any_inflow ? &c->bc : nullptr);
+    return initial_state(c, macros);
 }
 
 int kgs_iterate(kgs_ctx *c, int n_iters, int *done, double *residual)
@@ -586,7 +380,7 @@ int kgs_iterate(kgs_ctx *c, int n_iters, int *done, double *residual)
 int kgs_moments(kgs_ctx *c, double *out)
 {
     if (!c || !out) return KGS_EINVAL;
-    KGS_CHECK(cudaMemcpyAsync(out, c->mac, sizeof(double) * 8 * c->ncell, cudaMemcpyDeviceToHost, c->stream));
+    KGS_CHECK(cudaMemcpyAsync(out, c->mac, sizeof(double) * 8 * c->t.ncell, cudaMemcpyDeviceToHost, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     return KGS_OK;
 }
@@ -594,14 +388,15 @@ int kgs_moments(kgs_ctx *c, double *out)
 int kgs_moments_device(kgs_ctx *c, double *out_dev)
 {
     if (!c || !out_dev) return KGS_EINVAL;
-    KGS_CHECK(cudaMemcpyAsync(out_dev, c->mac, sizeof(double) * 8 * c->ncell, cudaMemcpyDeviceToDevice, c->stream));
+    KGS_CHECK(
+        cudaMemcpyAsync(out_dev, c->mac, sizeof(double) * 8 * c->t.ncell, cudaMemcpyDeviceToDevice, c->stream));
     return KGS_OK;
 }
 
 int kgs_rho_w(kgs_ctx *c, double *out)
 {
     if (!c || !out) return KGS_EINVAL;
-    KGS_CHECK(cudaMemcpyAsync(out, c->rho_w, sizeof(double) * 6 * c->ncell, cudaMemcpyDeviceToHost, c->stream));
+    KGS_CHECK(cudaMemcpyAsync(out, c->rho_w, sizeof(double) * 6 * c->t.ncell, cudaMemcpyDeviceToHost, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     return KGS_OK;
 }
@@ -609,7 +404,7 @@ int kgs_rho_w(kgs_ctx *c, double *out)
 int kgs_set_rho_w(kgs_ctx *c, const double *in)
 {
     if (!c || !in) return KGS_EINVAL;
-    KGS_CHECK(cudaMemcpyAsync(c->rho_w, in, sizeof(double) * 6 * c->ncell, cudaMemcpyHostToDevice, c->stream));
+    KGS_CHECK(cudaMemcpyAsync(c->rho_w, in, sizeof(double) * 6 * c->t.ncell, cudaMemcpyHostToDevice, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     return KGS_OK;
 }
@@ -625,18 +420,18 @@ struct CkptHeader {
 int kgs_save(kgs_ctx *c, void *buf, size_t *len)
 {
     if (!c || !len) return KGS_EINVAL;
-    const size_t need = sizeof(CkptHeader) + sizeof(double) * 14 * c->ncell;
+    const size_t n = c->t.ncell;
+    const size_t need = sizeof(CkptHeader) + sizeof(double) * 14 * n;
     if (!buf) {
         *len = need;
         return KGS_OK;
     }
     if (*len < need) return KGS_EINVAL;
-    CkptHeader h{CKPT_MAGIC, c->nx, c->ny, c->nz, c->Nv, c->iteration, c->M0, c->last_residual};
+    CkptHeader h{CKPT_MAGIC, c->t.nx, c->t.ny, c->t.nz, c->t.Nv, c->iteration, c->M0, c->last_residual};
     std::memcpy(buf, &h, sizeof h);
     double *body = reinterpret_cast<double *>(static_cast<char *>(buf) + sizeof h);
-    KGS_CHECK(cudaMemcpyAsync(body, c->mac, sizeof(double) * 8 * c->ncell, cudaMemcpyDeviceToHost, c->stream));
-    KGS_CHECK(cudaMemcpyAsync(body + 8 * c->ncell, c->rho_w, sizeof(double) * 6 * c->ncell, cudaMemcpyDeviceToHost,
-                              c->stream));
+    KGS_CHECK(cudaMemcpyAsync(body, c->mac, sizeof(double) * 8 * n, cudaMemcpyDeviceToHost, c->stream));
+    KGS_CHECK(cudaMemcpyAsync(body + 8 * n, c->rho_w, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     *len = need;
     return KGS_OK;
@@ -645,16 +440,16 @@ int kgs_save(kgs_ctx *c, void *buf, size_t *len)
 int kgs_load(kgs_ctx *c, const void *buf, size_t len)
 {
     if (!c || !buf) return KGS_EINVAL;
-    const size_t need = sizeof(CkptHeader) + sizeof(double) * 14 * c->ncell;
+    const size_t n = c->t.ncell;
+    const size_t need = sizeof(CkptHeader) + sizeof(double) * 14 * n;
     if (len != need) return KGS_EFORMAT;
     CkptHeader h;
     std::memcpy(&h, buf, sizeof h);
-    if (h.magic != CKPT_MAGIC || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.Nv != c->Nv)
+    if (h.magic != CKPT_MAGIC || h.nx != c->t.nx || h.ny != c->t.ny || h.nz != c->t.nz || h.Nv != c->t.Nv)
         return KGS_EFORMAT;
     const double *body = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof h);
-    KGS_CHECK(cudaMemcpyAsync(c->mac, body, sizeof(double) * 8 * c->ncell, cudaMemcpyHostToDevice, c->stream));
-    KGS_CHECK(cudaMemcpyAsync(c->rho_w, body + 8 * c->ncell, sizeof(double) * 6 * c->ncell, cudaMemcpyHostToDevice,
-                              c->stream));
+    KGS_CHECK(cudaMemcpyAsync(c->mac, body, sizeof(double) * 8 * n, cudaMemcpyHostToDevice, c->stream));
+    KGS_CHECK(cudaMemcpyAsync(c->rho_w, body + 8 * n, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     c->iteration = h.iteration;
     c->M0 = h.M0;
@@ -665,19 +460,20 @@ int kgs_load(kgs_ctx *c, const void *buf, size_t len)
 int kgs_info(kgs_ctx *c, kgs_info_t *o)
 {
     if (!c || !o) return KGS_EINVAL;
-    o->nx = c->nx;
-    o->ny = c->ny;
-    o->nz = c->nz;
-    o->nvx = c->nvx;
-    o->nvy = c->nvy;
-    o->nvz = c->nvz;
-    o->n_fluid = c->n_fluid;
-    o->phase_points = c->n_fluid * (long long)c->Nv;
+    const HostTables &t = c->t;
+    o->nx = t.nx;
+    o->ny = t.ny;
+    o->nz = t.nz;
+    o->nvx = t.nvx;
+    o->nvy = t.nvy;
+    o->nvz = t.nvz;
+    o->n_fluid = t.n_fluid;
+    o->phase_points = t.n_fluid * (long long)t.Nv;
     o->iteration = c->iteration;
-    o->n_stages = (int)c->stage_n.size();
-    o->v_per_cta = c->vg_size;
-    o->block_z = c->bz;
-    o->precision = c->precision;
+    o->n_stages = (int)t.stage_n.size();
+    o->v_per_cta = t.vg_size;
+    o->block_z = t.bz;
+    o->precision = t.precision;
     o->device_bytes = c->device_bytes;
     o->last_residual = c->last_residual;
     return KGS_OK;

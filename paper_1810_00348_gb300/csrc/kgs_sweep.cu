@@ -18,13 +18,24 @@
 // slice k-1 at (i, j) is read once, by the update of (i, j, k), just before
 // it is overwritten), with a halo row and column holding the values that
 // enter the slice from the upwind neighbour blocks or the domain boundary.
-// Each update is the pointwise solution of Eq. (7):
+// Within a slice a thread visits the cells by anti-diagonals i + j = d: the
+// cells of one diagonal are independent, so the fully unrolled diagonal loop
+// keeps up to eight update chains in flight, with the latest value of each
+// row held in registers.  Each update is the pointwise solution of Eq. (7):
 //     f = (f^S/tau + sum_d a_d f_up,d) / (1/tau + sum_d a_d),  a_d = |xi_d|/dx_d,
 // with the Shakhov equilibrium f^S of Eq. (2) computed on the fly from the
-// lagged coefficients of the cell.  After each slice the threads switch to a
-// cell-per-thread layout and sum the slice's moments over the group's
-// velocities (the 13 sums about the lagged velocity U^n and the incoming
-// wall fluxes of Eq. (9)); the per-(group, cell) partials go to global
+// lagged coefficients of the cell.
+//
+// After each slice the threads switch to a cell-per-thread layout and sum
+// the slice's moments over the group's velocities: the 13 sums about the
+// lagged velocity U^n and the incoming wall fluxes of Eq. (9).  Along an
+// x-line of the tensor-product velocity grid only c_x changes, so a thread
+// accumulates P_a = sum w_x c_x^a f (a = 0..3) and folds them with the line's
+// c_y, c_z and w_y w_z at the end of the line.  In FP32 the factors c_d =
+// xi_d - U_d are carried as float pairs (hi + lo, with first-order
+// corrections): their rounding would otherwise repeat identically on every
+// line and add up coherently in the heat flux.  The line folds go into
+// Kahan-compensated sums; the per-(group, cell) partial is written to global
 // memory in FP64 and a fixed-order reduction closes the iteration (no
 // atomics).  Block faces between stages go through three face planes in
 // global memory indexed by the cell position on the face: a block reads the
@@ -58,6 +69,16 @@ __device__ __forceinline__ float implicit_div(float num, float den) { return num
 
 __host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 
+// a - b = s + e exactly (Knuth's two-sum on a + (-b)).
+template <typename Real>
+__device__ __forceinline__ void two_diff(Real a, Real b, Real &s, Real &e)
+{
+    s = a - b;
+    const Real bv = s - a;
+    const Real av = s - bv;
+    e = (a - av) - (b + bv);
+}
+
 // Running sum for the per-thread moment accumulation.  FP32 sums carry a
 // Kahan compensation term (the value is sum - comp); FP64 sums are plain.
 template <typename Real>
@@ -81,28 +102,87 @@ struct RunSum<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
+constexpr int VT = 8;  // moment-phase velocity table entries per velocity
+
+// Four consecutive coefficients of a cell (one 16-byte shared load for FP32,
+// two for FP64).
+template <typename Real>
+struct Quad {
+    Real x, y, z, w;
+};
+__device__ __forceinline__ Quad<float> load_quad(const float *p)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Quad<double> load_quad(const double *p)
+{
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    return {a.x, a.y, b.x, b.y};
+}
+
 template <typename Real, int TV>
 struct SmemLayout {
     static constexpr int VG = NT * TV;
     static constexpr int CS = VG + 1;  // odd cell stride: conflict-free per-cell reads
     static constexpr size_t slice_bytes = align16(sizeof(Real) * (BY + 1) * (BX + 1) * CS);
     static constexpr size_t coef_bytes = align16(sizeof(Real) * SLICE * NCOEF);
-    static constexpr size_t vel_bytes = align16(sizeof(Real) * VG * 8);
+    static constexpr size_t vt_bytes = align16(sizeof(Real) * VG * VT);
     static constexpr size_t red_bytes = sizeof(double) * NPART * SLICE;
-    static constexpr size_t total = slice_bytes + coef_bytes + vel_bytes + red_bytes;
+    static constexpr size_t fixed = slice_bytes + coef_bytes + vt_bytes + red_bytes;
+    static int cx_stride(int nxm) { return nxm | 1; }  // odd: conflict-free per-cell reads
+    static size_t total(int nxm)
+    {
+        return fixed + align16(sizeof(Real) * 2 * nxm) + 2 * align16(sizeof(Real) * SLICE * cx_stride(nxm));
+    }
 };
 
-template <typename Real, int TV>
-__global__ void __launch_bounds__(NT) sweep_kernel(const SweepArgs a)
+// Coefficient prefetch: each thread moves 8 of the slice's SLICE*NCOEF values.
+constexpr int CPF = SLICE * NCOEF / NT;
+static_assert(CPF == 8, "coefficient prefetch assumes 8 values per thread");
+
+// Partial of one (group, cell) as stored in global memory: FP64, or the FP32
+// Kahan pair (sum, compensation) with value sum - compensation.
+template <typename Real>
+struct PartOut;
+template <>
+struct PartOut<double> {
+    using T = double;
+};
+template <>
+struct PartOut<float> {
+    using T = float2;
+};
+
+// (s0 - c0) + (s1 - c1) as a Kahan pair (s, c), value s - c, with an exact
+// two-sum of the leading parts.
+__device__ __forceinline__ float2 pair_add(float s0, float c0, float s1, float c1)
+{
+    const float S = s0 + s1;
+    const float bv = S - s0;
+    const float E = ((s0 - (S - bv)) + (s1 - bv)) - (c0 + c1);
+    const float hi = S + E;
+    const float lo = E - (hi - S);
+    return make_float2(hi, -lo);
+}
+
+template <typename Real, int TV, int LINE>
+__global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
 {
     using L = SmemLayout<Real, TV>;
     constexpr int VG = L::VG;
     constexpr int CS = L::CS;
     extern __shared__ __align__(16) unsigned char smem[];
+    const int nxm = a.nxo_max;
     Real *slice = reinterpret_cast<Real *>(smem);
     Real *cs = reinterpret_cast<Real *>(smem + L::slice_bytes);
-    Real *vs = reinterpret_cast<Real *>(smem + L::slice_bytes + L::coef_bytes);
-    double *mred = reinterpret_cast<double *>(smem + L::slice_bytes + L::coef_bytes + L::vel_bytes);
+    Real *vt = reinterpret_cast<Real *>(smem + L::slice_bytes + L::coef_bytes);
+    double *mred = reinterpret_cast<double *>(smem + L::slice_bytes + L::coef_bytes + L::vt_bytes);
+    const int cxs = nxm | 1;
+    Real *xn = reinterpret_cast<Real *>(smem + L::fixed);  // [nxm][2]
+    Real *cxh = reinterpret_cast<Real *>(smem + L::fixed + align16(sizeof(Real) * 2 * nxm));  // [SLICE][cxs]
+    Real *cxl = cxh + align16(sizeof(Real) * SLICE * cxs) / sizeof(Real);                    // [SLICE][cxs]
 
     const int t = threadIdx.x;
     const int4 w = a.work[blockIdx.x];
@@ -113,6 +193,7 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepArgs a)
     const int nvg = min(VG, vcount - v0);
     const int gvbase = a.oct_vstart[o] + v0;
     const int vgid = a.oct_vgbase[o] + blockIdx.y;
+    const int nxo = a.oct_nx[o];
 
     // Octant bit d set: xi_d >= 0, sweep towards +d.
     const bool px = (o & 1) != 0, py = (o & 2) != 0, pz = (o & 4) != 0;
@@ -124,28 +205,29 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepArgs a)
     const int z0 = bzi * a.bz, ez = min(a.bz, a.nz - z0);
     const bool xfirst = w.y == 0, yfirst = w.z == 0, zfirst = w.w == 0;
     const bool xlast = w.y == a.nbx - 1, ylast = w.z == a.nby - 1, zlast = w.w == a.nbz - 1;
-    const int sidex = px ? 0 : 1, sidey = py ? 2 : 3, sidez = pz ? 4 : 5;      // upwind sides
-    const int headx = px ? 1 : 0, heady = py ? 3 : 2, headz = pz ? 5 : 4;      // downwind sides
+    const int sidex = px ? 0 : 1, sidey = py ? 2 : 3, sidez = pz ? 4 : 5;  // upwind sides
+    const int headx = px ? 1 : 0, heady = py ? 3 : 2, headz = pz ? 5 : 4;  // downwind sides
     const int nx = a.nx, ny = a.ny;
     const size_t ncell = a.ncell;
     const size_t Nv = (size_t)a.Nv;
+    const bool any_solid = a.any_solid != 0;
 
     auto GX = [&](int li) { return px ? x0 + li : x0 + ex - 1 - li; };
     auto GY = [&](int lj) { return py ? y0 + lj : y0 + ey - 1 - lj; };
     auto GZ = [&](int lk) { return pz ? z0 + lk : z0 + ez - 1 - lk; };
     auto SL = [&](int li, int lj) { return ((lj + 1) * (BX + 1) + (li + 1)) * CS; };  // li, lj may be -1
+    auto CELL = [&](int x, int y, int z) { return (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z); };
 
     const Real *vel = static_cast<const Real *>(a.vel);
+    const Real *velm = static_cast<const Real *>(a.velm);
     const Real *mt = static_cast<const Real *>(a.mtab);
     const Real *coef = static_cast<const Real *>(a.coef);
     Real *FXp = static_cast<Real *>(a.FX);
     Real *FYp = static_cast<Real *>(a.FY);
     Real *FZp = static_cast<Real *>(a.FZ);
 
-    // Per-thread velocities: vl = t + m*NT.
-    const Real *velw = static_cast<const Real *>(a.velw);
-    const int nxo = a.oct_nx[o];
-    Real xi[TV][3], mgx[TV], mgy[TV], mgz[TV], msol[TV];
+    // ---- per-thread velocities (vl = t + m*NT) and the moment-phase tables ----
+    Real xi[TV][3], axi[TV][3], mgx[TV], mgy[TV], mgz[TV], msol[TV];
     size_t gv[TV];
     bool ok[TV];
     const int rowx = a.side_inflow[sidex] ? MT_INFLOW : sidex;
@@ -156,26 +238,32 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepArgs a)
         const int vl = t + m * NT;
         ok[m] = vl < nvg;
         gv[m] = (size_t)gvbase + (ok[m] ? vl : 0);
-        Real w4[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) w4[q] = vel[gv[m] * 4 + q];
-        xi[m][0] = w4[0];
-        xi[m][1] = w4[1];
-        xi[m][2] = w4[2];
-        // moment-phase table: xi_x, w_x, x-line end flag, -, xi_y, xi_z, w_y w_z, -
-        Real *vt = vs + vl * 8;
-        vt[0] = w4[0];
-        vt[1] = ok[m] ? velw[gv[m] * 2 + 0] : Real(0);
-        vt[2] = ((v0 + vl) % nxo == nxo - 1) ? Real(1) : Real(0);
-        vt[3] = Real(0);
-        vt[4] = w4[1];
-        vt[5] = w4[2];
-        vt[6] = ok[m] ? velw[gv[m] * 2 + 1] : Real(0);
-        vt[7] = Real(0);
+        xi[m][0] = vel[gv[m] * 4 + 0];
+        xi[m][1] = vel[gv[m] * 4 + 1];
+        xi[m][2] = vel[gv[m] * 4 + 2];
+        axi[m][0] = fabs(xi[m][0]);
+        axi[m][1] = fabs(xi[m][1]);
+        axi[m][2] = fabs(xi[m][2]);
+        // x-line factor w_x; line data for the fold: xi_y, xi_z (hi, lo), w_y w_z
+        Real *e = vt + vl * VT;
+        e[0] = ok[m] ? velm[gv[m] * 8 + 0] : Real(0);
+        e[1] = xi[m][1];
+        e[2] = xi[m][2];
+        e[3] = ok[m] ? velm[gv[m] * 8 + 1] : Real(0);
+        e[4] = velm[gv[m] * 8 + 3];
+        e[5] = velm[gv[m] * 8 + 4];
+        e[6] = Real(0);
+        e[7] = Real(0);
         mgx[m] = mt[(size_t)rowx * Nv + gv[m]];
         mgy[m] = mt[(size_t)rowy * Nv + gv[m]];
         mgz[m] = mt[(size_t)rowz * Nv + gv[m]];
         msol[m] = mt[(size_t)MT_SOLID * Nv + gv[m]];
+    }
+    // x nodes of the octant in line order (the first nxo velocities of the octant)
+    for (int ix = t; ix < nxo; ix += NT) {
+        const size_t g = (size_t)a.oct_vstart[o] + ix;
+        xn[ix * 2 + 0] = vel[g * 4 + 0];
+        xn[ix * 2 + 1] = velm[g * 8 + 2];
     }
 
     // Ghost value entering through domain side `side` at cell `cell`:
@@ -189,104 +277,144 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepArgs a)
         const int li = cl % BX, lj = cl / BX;
         if (li >= ex || lj >= ey) continue;
         const int x = GX(li), y = GY(lj), z = GZ(0);
-        const size_t cell = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
-        const Real rw = zfirst ? wall_rho(sidez, cell) : Real(0);
+        const Real rw = zfirst ? wall_rho(sidez, CELL(x, y, z)) : Real(0);
 #pragma unroll
         for (int m = 0; m < TV; m++) {
             if (!ok[m]) continue;
-            Real v = zfirst ? rw * mgz[m] : FZp[((size_t)y * nx + x) * Nv + gv[m]];
+            const Real v = zfirst ? rw * mgz[m] : FZp[((size_t)y * nx + x) * Nv + gv[m]];
             slice[SL(li, lj) + t + m * NT] = v;
         }
     }
 
+    // ---- prefetch registers: coefficients and halos of one slice ----
+    Real pc[CPF];
+    Real phx[BY][TV], phy[BX][TV];
+    auto prefetch = [&](int lk) {
+        const int z = GZ(lk);
+        const int cl = (t * CPF) / NCOEF, q0 = (t * CPF) % NCOEF;
+        const int li = cl % BX, lj = cl / BX;
+        if (li < ex && lj < ey) {
+            const Real *src = coef + CELL(GX(li), GY(lj), z) * NCOEF + q0;
+#pragma unroll
+            for (int q = 0; q < CPF; q++) pc[q] = src[q];
+        } else {
+#pragma unroll
+            for (int q = 0; q < CPF; q++) pc[q] = (q0 + q == C_FLAGS) ? Real(F_SOLID) : Real(0);
+        }
+#pragma unroll
+        for (int lj2 = 0; lj2 < BY; lj2++) {
+            if (lj2 >= ey) break;
+            const int y = GY(lj2), x = GX(0);
+            const Real rw = xfirst ? wall_rho(sidex, CELL(x, y, z)) : Real(0);
+#pragma unroll
+            for (int m = 0; m < TV; m++)
+                phx[lj2][m] = xfirst ? rw * mgx[m] : (ok[m] ? FXp[((size_t)z * ny + y) * Nv + gv[m]] : Real(0));
+        }
+#pragma unroll
+        for (int li2 = 0; li2 < BX; li2++) {
+            if (li2 >= ex) break;
+            const int x = GX(li2), y = GY(0);
+            const Real rw = yfirst ? wall_rho(sidey, CELL(x, y, z)) : Real(0);
+#pragma unroll
+            for (int m = 0; m < TV; m++)
+                phy[li2][m] = yfirst ? rw * mgy[m] : (ok[m] ? FYp[((size_t)z * nx + x) * Nv + gv[m]] : Real(0));
+        }
+    };
+    prefetch(0);
+
     for (int lk = 0; lk < ez; lk++) {
         const int z = GZ(lk);
-        __syncthreads();  // the previous slice's moment phase is done with smem
-        // coefficients of the slice's cells (invalid cells flagged solid)
-        for (int idx = t; idx < SLICE * NCOEF; idx += NT) {
-            const int cl = idx / NCOEF, q = idx % NCOEF;
-            const int li = cl % BX, lj = cl / BX;
-            Real v;
-            if (li < ex && lj < ey) {
-                const size_t cell = (size_t)GX(li) + (size_t)nx * ((size_t)GY(lj) + (size_t)ny * z);
-                v = coef[cell * NCOEF + q];
-            } else {
-                v = (q == C_FLAGS) ? Real(F_SOLID) : Real(0);
-            }
-            cs[idx] = v;
-        }
-        // halo column (x inflow) and halo row (y inflow) of this slice
-        for (int lj = 0; lj < ey; lj++) {
-            const int y = GY(lj), x = GX(0);
-            const size_t cell = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
-            const Real rw = xfirst ? wall_rho(sidex, cell) : Real(0);
+        // stage the prefetched slice data in shared memory
 #pragma unroll
-            for (int m = 0; m < TV; m++) {
-                if (!ok[m]) continue;
-                Real v = xfirst ? rw * mgx[m] : FXp[((size_t)z * ny + y) * Nv + gv[m]];
-                slice[SL(-1, lj) + t + m * NT] = v;
-            }
-        }
-        for (int li = 0; li < ex; li++) {
-            const int x = GX(li), y = GY(0);
-            const size_t cell = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
-            const Real rw = yfirst ? wall_rho(sidey, cell) : Real(0);
+        for (int q = 0; q < CPF; q++) cs[t * CPF + q] = pc[q];
 #pragma unroll
-            for (int m = 0; m < TV; m++) {
-                if (!ok[m]) continue;
-                Real v = yfirst ? rw * mgy[m] : FYp[((size_t)z * nx + x) * Nv + gv[m]];
-                slice[SL(li, -1) + t + m * NT] = v;
-            }
+        for (int lj = 0; lj < BY; lj++) {
+            if (lj >= ey) break;
+#pragma unroll
+            for (int m = 0; m < TV; m++)
+                if (ok[m]) slice[SL(-1, lj) + t + m * NT] = phx[lj][m];
+        }
+#pragma unroll
+        for (int li = 0; li < BX; li++) {
+            if (li >= ex) break;
+#pragma unroll
+            for (int m = 0; m < TV; m++)
+                if (ok[m]) slice[SL(li, -1) + t + m * NT] = phy[li][m];
         }
         __syncthreads();
+        // c_x = xi_x - U_x of each cell of the slice as a float pair, per x node
+        {
+            const int cl = t % SLICE, vp = t / SLICE;
+            const Real ux = cs[cl * NCOEF + C_UX];
+            for (int ix = vp; ix < nxo; ix += NT / SLICE) {
+                Real s, e;
+                two_diff(xn[ix * 2], ux, s, e);
+                cxh[cl * cxs + ix] = s;
+                cxl[cl * cxs + ix] = e + xn[ix * 2 + 1];
+            }
+        }
+        if (lk + 1 < ez) prefetch(lk + 1);
 
-        // ---- sweep of the slice: Eq. (2) fused into Eq. (7) ----
-        for (int lj = 0; lj < ey; lj++) {
-            const int y = GY(lj);
-            Real fprev[TV];
+        // ---- sweep of the slice: Eq. (2) fused into Eq. (7), by anti-diagonals ----
+        // The upwind values of cell (i, j) are read from the in-place slice:
+        // (i-1, j) and (i, j-1) were updated on the previous diagonal, (i, j)
+        // itself still holds slice k-1.  The cells of one diagonal are
+        // independent, which gives up to BY update chains in flight.
+        for (int d = 0; d < ex + ey - 1; d++) {
+            const int jhi = min(ey - 1, d), jlo = max(0, d - (ex - 1));
 #pragma unroll
-            for (int m = 0; m < TV; m++) fprev[m] = slice[SL(-1, lj) + t + m * NT];
-            for (int li = 0; li < ex; li++) {
-                const Real *c = cs + (lj * BX + li) * NCOEF;
-                const int flags = (int)c[C_FLAGS];
-                if (flags & F_SOLID) continue;
-                const Real ux = c[C_UX], uy = c[C_UY], uz = c[C_UZ];
-                const Real kappa = c[C_KAPPA], nexp = c[C_NEXP], rt1 = c[C_RT1];
-                const Real qx = c[C_QX], qy = c[C_QY], qz = c[C_QZ];
-                const Real rtau = c[C_RTAU], rdx = c[C_RDX], rdy = c[C_RDY], rdz = c[C_RDZ];
-                const int x = GX(li);
-                const size_t cell = (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z);
-                const bool sol_x = flags & (F_SOLID_SIDE << sidex);
-                const bool sol_y = flags & (F_SOLID_SIDE << sidey);
-                const bool sol_z = flags & (F_SOLID_SIDE << sidez);
-                Real rwx = 0, rwy = 0, rwz = 0;
-                if (sol_x) rwx = Real(a.rho_w[sidex * ncell + cell]);
-                if (sol_y) rwy = Real(a.rho_w[sidey * ncell + cell]);
-                if (sol_z) rwz = Real(a.rho_w[sidez * ncell + cell]);
-                const int sidx = SL(li, lj);
+            for (int k = 0; k < BY; k++) {
+                const int lj = jhi - k;
+                if (lj >= jlo) {
+                    const int li = d - lj;
+                    const Real *c = cs + (lj * BX + li) * NCOEF;
+                    const Quad<Real> c0 = load_quad(c), c1 = load_quad(c + 4), c2v = load_quad(c + 8),
+                                     c3 = load_quad(c + 12);
+                    const Real ux = c0.x, uy = c0.y, uz = c0.z, kappa = c0.w;
+                    const Real nexp = c1.x, rt1 = c1.y, rtau = c1.z;
+                    const int flags = (int)c1.w;
+                    const Real qx = c2v.x, qy = c2v.y, qz = c2v.z, rdx = c2v.w;
+                    const Real rdy = c3.x, rdz = c3.y;
+                    if (!(flags & F_SOLID)) {
+                        bool sol_x = false, sol_y = false, sol_z = false;
+                        Real rwx = 0, rwy = 0, rwz = 0;
+                        if (any_solid) {
+                            const size_t cell = CELL(GX(li), GY(lj), z);
+                            sol_x = flags & (F_SOLID_SIDE << sidex);
+                            sol_y = flags & (F_SOLID_SIDE << sidey);
+                            sol_z = flags & (F_SOLID_SIDE << sidez);
+                            if (sol_x) rwx = Real(a.rho_w[sidex * ncell + cell]);
+                            if (sol_y) rwy = Real(a.rho_w[sidey * ncell + cell]);
+                            if (sol_z) rwz = Real(a.rho_w[sidez * ncell + cell]);
+                        }
+                        const int sidx = SL(li, lj);
+                        const bool out_x = li == ex - 1 && !xlast, out_y = lj == ey - 1 && !ylast;
 #pragma unroll
-                for (int m = 0; m < TV; m++) {
-                    const int vl = t + m * NT;
-                    Real fz = slice[sidx + vl];
-                    Real fy = slice[sidx - (BX + 1) * CS + vl];
-                    Real fx = fprev[m];
-                    if (sol_x) fx = rwx * msol[m];
-                    if (sol_y) fy = rwy * msol[m];
-                    if (sol_z) fz = rwz * msol[m];
-                    const Real cx = xi[m][0] - ux, cy = xi[m][1] - uy, cz = xi[m][2] - uz;
-                    const Real c2 = cx * cx + cy * cy + cz * cz;
-                    const Real cq = cx * qx + cy * qy + cz * qz;
-                    const Real E = eq_exp(c2 * nexp);
-                    const Real src = kappa * E * (Real(1) + cq * (c2 * rt1 - Real(5)));
-                    const Real ax = fabs(xi[m][0]) * rdx, ay = fabs(xi[m][1]) * rdy, az = fabs(xi[m][2]) * rdz;
-                    const Real num = src + ax * fx + ay * fy + az * fz;
-                    const Real den = rtau + ax + ay + az;
-                    const Real f = implicit_div(num, den);
-                    fprev[m] = f;
-                    if (ok[m]) {
-                        slice[sidx + vl] = f;
-                        if (li == ex - 1 && !xlast) FXp[((size_t)z * ny + y) * Nv + gv[m]] = f;
-                        if (lj == ey - 1 && !ylast) FYp[((size_t)z * nx + x) * Nv + gv[m]] = f;
+                        for (int m = 0; m < TV; m++) {
+                            const int vl = t + m * NT;
+                            Real fz = slice[sidx + vl];
+                            Real fy = slice[sidx - (BX + 1) * CS + vl];
+                            Real fx = slice[sidx - CS + vl];
+                            if (any_solid) {
+                                if (sol_x) fx = rwx * msol[m];
+                                if (sol_y) fy = rwy * msol[m];
+                                if (sol_z) fz = rwz * msol[m];
+                            }
+                            const Real cx = xi[m][0] - ux, cy = xi[m][1] - uy, cz = xi[m][2] - uz;
+                            const Real c2 = cx * cx + cy * cy + cz * cz;
+                            const Real cq = cx * qx + cy * qy + cz * qz;
+                            const Real E = eq_exp(c2 * nexp);
+                            const Real src = kappa * E * (Real(1) + cq * (c2 * rt1 - Real(5)));
+                            const Real ax = axi[m][0] * rdx, ay = axi[m][1] * rdy, az = axi[m][2] * rdz;
+                            const Real num = src + ax * fx + ay * fy + az * fz;
+                            const Real den = rtau + ax + ay + az;
+                            const Real f = implicit_div(num, den);
+                            if (ok[m]) {
+                                slice[sidx + vl] = f;
+                                if (out_x) FXp[((size_t)z * ny + GY(lj)) * Nv + gv[m]] = f;
+                                if (out_y) FYp[((size_t)z * nx + GX(li)) * Nv + gv[m]] = f;
+                            }
+                        }
                     }
                 }
             }
@@ -294,92 +422,145 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepArgs a)
         __syncthreads();
 
         // ---- moments of the slice over the group's velocities ----
-        // Thread (cell, half) sums its half of the group's velocities.  The
-        // velocities come in x-lines of the tensor-product grid (ix fastest):
-        // along a line only c_x changes, so the thread keeps the four line
-        // sums P_a = sum w_x c_x^a f (a = 0..3) and, at the end of each line,
-        // folds them with the line's c_y, c_z, w_y w_z into the 13 sums about
-        // U^n and the three incoming wall fluxes (Eq. (5), Eq. (9)).
         {
             const int cl = t % SLICE, vp = t / SLICE;  // NT = 2 * SLICE: two velocity halves
             const int li = cl % BX, lj = cl / BX;
             const bool valid = li < ex && lj < ey;
-            double acc[NPART];
+            const Real *c = cs + cl * NCOEF;
+            const int flags = (int)c[C_FLAGS + 0];
+            RunSum<Real> S[NPART];
+            if (valid && !(flags & F_SOLID)) {
+                const Real ux = c[C_UX], uy = c[C_UY], uz = c[C_UZ];
+                const bool wx = flags & (F_WALL_SIDE << headx);
+                const bool wy = flags & (F_WALL_SIDE << heady);
+                const bool wz = flags & (F_WALL_SIDE << headz);
+                const Real sgnx = px ? Real(1) : Real(-1);
+                const Real *sp = slice + SL(li, lj);
+                const int vbeg = vp * (VG / 2);
+                const int vend = min(vbeg + VG / 2, nvg);
+                // fold the line sums P_a (x-line of the tensor-product grid ending at
+                // velocity ve-1) with the line's c_y, c_z and w_y w_z
+                auto fold = [&](Real P0, Real P1, Real P2, Real P3, int ve) {
+                    const Real *e = vt + (ve - 1) * VT;
+                    Real cy, cyl, cz, czl;
+                    two_diff(e[1], uy, cy, cyl);
+                    two_diff(e[2], uz, cz, czl);
+                    cyl += e[4];
+                    czl += e[5];
+                    const Real W = e[3];
+                    const Real q0 = W * P0, q1 = W * P1, q2 = W * P2;
+                    const Real r2 = fma(cy, cy, cz * cz);
+                    const Real r2l = Real(2) * fma(cy, cyl, cz * czl);
+                    S[P_S0].add(q0);
+                    S[P_S1X].add(q1);
+                    S[P_S1Y].add(fma(cy, q0, cyl * q0));
+                    S[P_S1Z].add(fma(cz, q0, czl * q0));
+                    S[P_S2XX].add(q2);
+                    S[P_S2YY].add(fma(cy, cy, Real(2) * cy * cyl) * q0);
+                    S[P_S2ZZ].add(fma(cz, cz, Real(2) * cz * czl) * q0);
+                    S[P_S2XY].add(fma(cy, q1, cyl * q1));
+                    S[P_S2XZ].add(fma(cz, q1, czl * q1));
+                    S[P_S2YZ].add(fma(cy, cz, fma(cyl, cz, cy * czl)) * q0);
+                    S[P_S3X].add(fma(W, P3, fma(r2, q1, r2l * q1)));
+                    const Real e2 = fma(r2, q0, fma(r2l, q0, q2));
+                    S[P_S3Y].add(fma(cy, e2, cyl * e2));
+                    S[P_S3Z].add(fma(cz, e2, czl * e2));
+                    // incoming flux w |xi_d| f towards the wall ahead
+                    if (wx) S[P_FX].add(sgnx * fma(ux, q0, q1));
+                    if (wy) S[P_FY].add(fabs(e[1]) * q0);
+                    if (wz) S[P_FZ].add(fabs(e[2]) * q0);
+                };
+                if constexpr (LINE > 0) {
+                    // Every x-line has LINE nodes and the thread's range holds whole
+                    // lines: the c_x pairs and w_x of the LINE nodes stay in registers.
+                    Real cxr[LINE], cxlr[LINE], wxr[LINE];
 #pragma unroll
-            for (int q = 0; q < NPART; q++) acc[q] = 0.0;
-            if (valid) {
-                const Real *c = cs + cl * NCOEF;
-                const int flags = (int)c[C_FLAGS];
-                if (!(flags & F_SOLID)) {
-                    const Real ux = c[C_UX], uy = c[C_UY], uz = c[C_UZ];
-                    const bool wx = flags & (F_WALL_SIDE << headx);
-                    const bool wy = flags & (F_WALL_SIDE << heady);
-                    const bool wz = flags & (F_WALL_SIDE << headz);
-                    const Real sgnx = px ? Real(1) : Real(-1);
-                    RunSum<Real> S[NPART];
-                    Real P0 = 0, P1 = 0, P2 = 0, P3 = 0;
-                    const Real *sp = slice + SL(li, lj);
-                    const int vbeg = vp * (VG / 2);
-                    const int vend = min(vbeg + VG / 2, nvg);
-                    for (int v = vbeg; v < vend; v++) {
-                        const Real f = sp[v];
-                        const Real *vt = vs + v * 8;
-                        const Real cx = vt[0] - ux;
-                        const Real t0 = vt[1] * f;
-                        const Real t1 = t0 * cx;
-                        const Real t2 = t1 * cx;
-                        P0 += t0;
-                        P1 += t1;
-                        P2 += t2;
-                        P3 += t2 * cx;
-                        if (vt[2] != Real(0) || v == vend - 1) {  // end of an x-line (warp-uniform)
-                            const Real cy = vt[4] - uy, cz = vt[5] - uz, W = vt[6];
-                            const Real q0 = W * P0, q1 = W * P1, q2 = W * P2;
-                            const Real r2 = cy * cy + cz * cz;
-                            S[P_S0].add(q0);
-                            S[P_S1X].add(q1);
-                            S[P_S1Y].add(cy * q0);
-                            S[P_S1Z].add(cz * q0);
-                            S[P_S2XX].add(q2);
-                            S[P_S2YY].add(cy * cy * q0);
-                            S[P_S2ZZ].add(cz * cz * q0);
-                            S[P_S2XY].add(cy * q1);
-                            S[P_S2XZ].add(cz * q1);
-                            S[P_S2YZ].add(cy * cz * q0);
-                            S[P_S3X].add(W * P3 + r2 * q1);
-                            const Real e2 = q2 + r2 * q0;
-                            S[P_S3Y].add(cy * e2);
-                            S[P_S3Z].add(cz * e2);
-                            // incoming flux w |xi_d| f towards the wall ahead
-                            if (wx) S[P_FX].add(sgnx * (q1 + ux * q0));
-                            if (wy) S[P_FY].add(fabs(vt[4]) * q0);
-                            if (wz) S[P_FZ].add(fabs(vt[5]) * q0);
-                            P0 = P1 = P2 = P3 = Real(0);
-                        }
+                    for (int ix = 0; ix < LINE; ix++) {
+                        Real hi, lo;
+                        two_diff(xn[ix * 2], ux, hi, lo);
+                        cxr[ix] = hi;
+                        cxlr[ix] = lo + xn[ix * 2 + 1];
+                        wxr[ix] = vt[(vbeg + ix) * VT];
                     }
+                    for (int v = vbeg; v < vend; v += LINE) {
+                        Real P0 = 0, P1 = 0, P2 = 0, P3 = 0, C1 = 0, C2 = 0, C3 = 0;
 #pragma unroll
-                    for (int q = 0; q < NPART; q++) acc[q] = S[q].value();
+                        for (int ix = 0; ix < LINE; ix++) {
+                            const Real f = sp[v + ix];
+                            const Real cx = cxr[ix];
+                            const Real t0 = wxr[ix] * f;
+                            const Real t1 = t0 * cx;
+                            const Real t2 = t1 * cx;
+                            P0 += t0;
+                            P1 += t1;
+                            P2 += t2;
+                            P3 = fma(t2, cx, P3);
+                            C1 = fma(t0, cxlr[ix], C1);
+                            C2 = fma(t1, cxlr[ix], C2);
+                            C3 = fma(t2, cxlr[ix], C3);
+                        }
+                        // first-order corrections for the low part of c_x
+                        fold(P0, P1 + C1, fma(Real(2), C2, P2), fma(Real(3), C3, P3), v + LINE);
+                    }
+                } else {
+                    const Real *cxhc = cxh + cl * cxs, *cxlc = cxl + cl * cxs;
+                    int v = vbeg;
+                    while (v < vend) {
+                        // one x-line segment [v, ve): velocities with the same (xi_y, xi_z)
+                        const int ix0 = (v0 + v) % nxo;
+                        const int ve = min(vend, v + (nxo - ix0));
+                        Real P0 = 0, P1 = 0, P2 = 0, P3 = 0, C1 = 0, C2 = 0, C3 = 0;
+#pragma unroll 4
+                        for (int vv = v; vv < ve; vv++) {
+                            const int ix = ix0 + (vv - v);
+                            const Real f = sp[vv];
+                            const Real cx = cxhc[ix], cxlo = cxlc[ix];
+                            const Real t0 = vt[vv * VT] * f;
+                            const Real t1 = t0 * cx;
+                            const Real t2 = t1 * cx;
+                            P0 += t0;
+                            P1 += t1;
+                            P2 += t2;
+                            P3 = fma(t2, cx, P3);
+                            C1 = fma(t0, cxlo, C1);
+                            C2 = fma(t1, cxlo, C2);
+                            C3 = fma(t2, cxlo, C3);
+                        }
+                        fold(P0, P1 + C1, fma(Real(2), C2, P2), fma(Real(3), C3, P3), ve);
+                        v = ve;
+                    }
                 }
             }
+            // combine the two halves and write the (group, cell) partial
+            using Out = typename PartOut<Real>::T;
+            Out *red = reinterpret_cast<Out *>(mred);
             if (vp == 1) {
 #pragma unroll
-                for (int q = 0; q < NPART; q++) mred[q * SLICE + cl] = acc[q];
+                for (int q = 0; q < NPART; q++) {
+                    if constexpr (sizeof(Real) == 8)
+                        red[q * SLICE + cl] = S[q].value();
+                    else
+                        red[q * SLICE + cl] = make_float2(S[q].s, S[q].c);
+                }
             }
             __syncthreads();
             if (vp == 0 && valid) {
-                const size_t cell = (size_t)GX(li) + (size_t)nx * ((size_t)GY(lj) + (size_t)ny * z);
-                double *pp = a.part + (size_t)vgid * NPART * ncell + cell;
+                Out *pp = static_cast<Out *>(a.part) + (size_t)vgid * NPART * ncell + CELL(GX(li), GY(lj), z);
 #pragma unroll
-                for (int q = 0; q < NPART; q++) pp[(size_t)q * ncell] = acc[q] + mred[q * SLICE + cl];
+                for (int q = 0; q < NPART; q++) {
+                    if constexpr (sizeof(Real) == 8) {
+                        pp[(size_t)q * ncell] = S[q].value() + red[q * SLICE + cl];
+                    } else {
+                        const float2 o2 = red[q * SLICE + cl];
+                        pp[(size_t)q * ncell] = pair_add(S[q].s, S[q].c, o2.x, o2.y);
+                    }
+                }
             }
         }
     }
 
-    // z outflow of the block for the next stage
+    // z outflow of the block for the next stage (own velocities only)
     if (!zlast) {
-        __syncthreads();
-        const int z = GZ(ez - 1);
-        (void)z;
         for (int cl = 0; cl < SLICE; cl++) {
             const int li = cl % BX, lj = cl / BX;
             if (li >= ex || lj >= ey) continue;
@@ -393,36 +574,44 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const SweepArgs a)
     }
 }
 
-template <typename Real, int TV>
+template <typename Real, int TV, int LINE>
 cudaError_t launch_t(const SweepArgs &a, int n_items, int max_vg, cudaStream_t s)
 {
     using L = SmemLayout<Real, TV>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Real, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L::total);
+    static size_t configured = 0;
+    const size_t bytes = L::total(a.nxo_max);
+    if (bytes > configured) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Real, TV, LINE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured = bytes;
     }
     dim3 grid(n_items, max_vg);
-    sweep_kernel<Real, TV><<<grid, NT, L::total, s>>>(a);
+    sweep_kernel<Real, TV, LINE><<<grid, NT, bytes, s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename Real, int TV>
+cudaError_t launch_line(const SweepArgs &a, int n_items, int max_vg, cudaStream_t s)
+{
+    if (a.line16) return launch_t<Real, TV, 16>(a, n_items, max_vg, s);
+    return launch_t<Real, TV, 0>(a, n_items, max_vg, s);
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int precision, int tv)
+size_t sweep_smem_bytes(int precision, int tv, int nxo_max)
 {
-    if (precision == 0) return SmemLayout<double, 1>::total;
-    return tv == 2 ? SmemLayout<float, 2>::total : SmemLayout<float, 1>::total;
+    if (precision == 0) return SmemLayout<double, 1>::total(nxo_max);
+    return tv == 2 ? SmemLayout<float, 2>::total(nxo_max) : SmemLayout<float, 1>::total(nxo_max);
 }
 
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s)
 {
     if (n_items == 0 || max_vg == 0) return cudaSuccess;
-    if (precision == 0) return launch_t<double, 1>(a, n_items, max_vg, s);
-    if (tv == 2) return launch_t<float, 2>(a, n_items, max_vg, s);
-    return launch_t<float, 1>(a, n_items, max_vg, s);
+    if (precision == 0) return launch_line<double, 1>(a, n_items, max_vg, s);
+    if (tv == 2) return launch_line<float, 2>(a, n_items, max_vg, s);
+    return launch_line<float, 1>(a, n_items, max_vg, s);
 }
 
 }  // namespace kgs
