@@ -201,6 +201,43 @@ int kgs_profile(kgs_ctx *ctx, double *sweep_ms, long long *sweep_launches, long 
 void kgs_destroy(kgs_ctx *ctx);
 const char *kgs_strerror(int code);
 
+/* ---- iteration without device allocation ----
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory themselves or through this library:
+ * code running inside a framework whose pool owns all device memory, code on
+ * a latency-critical path that cannot afford cudaMalloc's implicit
+ * synchronisation, or code that must never allocate after start-up.
+ *
+ * One outer iteration of the problem described by the same structs as
+ * kgs_setup, from the state (macros_in [8][nz][ny][nx], rho_w_in
+ * [6][nz][ny][nx], device, FP64) to (macros_out, rho_w_out, device, FP64,
+ * caller-owned, distinct from the inputs), on `stream` (cudaStream_t, NULL =
+ * legacy default stream) of the current device.  M0 > 0 rescales the total
+ * mass to M0 (Section 3.4); M0 <= 0 skips the rescale.  precision and
+ * wall_norm as in kgs_opts; the velocities per thread block and the block
+ * depth take their defaults.  *residual (host, may be NULL) receives the
+ * Section 4.1 residual of the step.  The call returns after the iteration has
+ * completed on the GPU.
+ *
+ * No cudaMalloc, cudaFree or other allocating routine is called: every
+ * intermediate buffer lives in one file-scope device array of
+ * KGS_NOALLOC_SCRATCH_BYTES bytes that every GPU loading this library holds
+ * until the process exits.  Problems whose buffers do not fit are rejected
+ * with KGS_EINVAL (roughly: face planes (nx ny + ny nz + nz nx) * nvel and
+ * moment partials 8 * 16 * ncell * ceil(nvel_octant / 128) words must fit).
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the array and each call overwrites it: calls that overlap on the GPU
+ * (concurrent streams or host threads) race and must be serialised by the
+ * caller.
+ * Returns KGS_OK, KGS_EDIVERGED (outputs hold the offending iterate),
+ * KGS_EINVAL, KGS_ECUDA. */
+#define KGS_NOALLOC_SCRATCH_BYTES (64u << 20)
+int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vgrid, const kgs_gas *gas,
+                        const kgs_bc *bc, int precision, int wall_norm, double M0, const double *macros_in,
+                        const double *rho_w_in, double *macros_out, double *rho_w_out, double *residual,
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,11 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_longlong)]),
     "kgs_destroy": (None, [ctypes.c_void_p]),
     "kgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "kgs_iterate_noalloc": (ctypes.c_int, [ctypes.POINTER(KgsGrid), ctypes.POINTER(ctypes.c_uint8),
+                                           ctypes.POINTER(KgsVgrid), ctypes.POINTER(KgsGas), ctypes.POINTER(KgsBc),
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _dp,
+                                           ctypes.c_void_p]),
 }
 
 _lib = None
@@ -140,10 +145,9 @@ class Context:
         return (self.prob.nz, self.prob.ny, self.prob.nx)
 
 
-def kgs_setup(prob, precision=KGS_FP64, max_iters=1000, tol=1e-8, v_per_cta=0, block_z=0, stream=None):
-    """kgs_setup for an ``inputs.Problem``; stream is a cudaStream_t value (int) or None."""
-    lib = load()
-    keep = []
+def _problem_structs(prob, keep):
+    """ABI structs (grid, vgrid, gas, bc, solid pointer) of an inputs.Problem;
+    arrays referenced by pointers are appended to ``keep``."""
 
     def p(a):
         a = _arr(a)
@@ -163,13 +167,21 @@ def kgs_setup(prob, precision=KGS_FP64, max_iters=1000, tol=1e-8, v_per_cta=0, b
     bc.rho_in, bc.T_in, bc.T_solid = prob.rho_in, prob.T_in, prob.T_solid
     for d in range(3):
         bc.U_in[d] = float(prob.U_in[d])
-    opts = KgsOpts(precision, int(prob.wall_mode), int(prob.mass_rescale), max_iters, tol, v_per_cta, block_z,
-                   ctypes.c_void_p(stream) if stream else None)
     solid_p = ctypes.POINTER(ctypes.c_uint8)()
     if prob.solid is not None:
         sol = _arr(prob.solid, np.uint8).reshape(-1)
         keep.append(sol)
         solid_p = sol.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    return g, v, gas, bc, solid_p
+
+
+def kgs_setup(prob, precision=KGS_FP64, max_iters=1000, tol=1e-8, v_per_cta=0, block_z=0, stream=None):
+    """kgs_setup for an ``inputs.Problem``; stream is a cudaStream_t value (int) or None."""
+    lib = load()
+    keep = []
+    g, v, gas, bc, solid_p = _problem_structs(prob, keep)
+    opts = KgsOpts(precision, int(prob.wall_mode), int(prob.mass_rescale), max_iters, tol, v_per_cta, block_z,
+                   ctypes.c_void_p(stream) if stream else None)
     h = ctypes.c_void_p()
     _check(lib.kgs_setup(ctypes.byref(h), ctypes.byref(g), solid_p, ctypes.byref(v), ctypes.byref(gas),
                          ctypes.byref(bc), ctypes.byref(opts)), "kgs_setup")
@@ -277,3 +289,20 @@ def kgs_load_ptr(ctx, ptr, nbytes):
 
 def kgs_moments_ptr(ctx, ptr):
     return _check(load().kgs_moments(ctx.handle, ctypes.cast(ctypes.c_void_p(ptr), _dp)), "kgs_moments")
+
+
+def kgs_iterate_noalloc(prob, macros_in, rho_w_in, macros_out, rho_w_out, M0=0.0, precision=KGS_FP64,
+                        stream=None):
+    """kgs_iterate_noalloc with device pointers (ints) for the four state
+    buffers; returns (rc, residual).  KGS_EDIVERGED is returned, other errors
+    raise."""
+    keep = []
+    g, v, gas, bc, solid_p = _problem_structs(prob, keep)
+    res = ctypes.c_double(0.0)
+    rc = load().kgs_iterate_noalloc(ctypes.byref(g), solid_p, ctypes.byref(v), ctypes.byref(gas),
+                                    ctypes.byref(bc), int(precision), int(prob.wall_mode), float(M0),
+                                    ctypes.c_void_p(macros_in), ctypes.c_void_p(rho_w_in),
+                                    ctypes.c_void_p(macros_out), ctypes.c_void_p(rho_w_out), ctypes.byref(res),
+                                    ctypes.c_void_p(stream) if stream else None)
+    _check(rc, "kgs_iterate_noalloc", allow=(KGS_EDIVERGED,))
+    return rc, res.value
