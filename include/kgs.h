@@ -201,6 +201,71 @@ int kgs_profile(kgs_ctx *ctx, double *sweep_ms, long long *sweep_launches, long 
 void kgs_destroy(kgs_ctx *ctx);
 const char *kgs_strerror(int code);
 
+/* ---- batches of independent problems ----
+ * Many instances (e.g. cavities of uneven grid and velocity sizes) advanced
+ * together.  Each outer iteration of the batch is one persistent sweep launch
+ * over the work items of every active instance (instance, octant, velocity
+ * group, block, in wavefront-stage order; a thread block waits, with a
+ * bounded spin, for the three upwind blocks of its item), wrapped with the
+ * per-instance coefficient and closure kernels and replayed as a CUDA graph.
+ * Iterates exactly like kgs_iterate on each instance (same arithmetic, same
+ * results). */
+typedef struct kgs_batch kgs_batch;
+
+typedef struct {
+    kgs_grid grid;
+    const uint8_t *solid;     /* nx*ny*nz bytes or NULL */
+    kgs_vgrid vgrid;
+    kgs_gas gas;
+    kgs_bc bc;
+    int wall_norm;            /* KGS_WALL_DISCRETE / KGS_WALL_ANALYTIC */
+    int mass_rescale;
+} kgs_problem;
+
+/* Sweep shape (velocities per thread block, block depth along z) of one
+ * problem, chosen by timing a few outer iterations of each candidate on the
+ * current device; cached per problem shape in the process and, when the
+ * environment variable KGS_AUTOTUNE_CACHE names a file, in that file.
+ * Allocates and frees a context per candidate. */
+int kgs_autotune(const kgs_problem *prob, int precision, int *v_per_cta, int *block_z);
+
+/* Build a batch of n instances (inputs copied; each instance starts from the
+ * uniform state like kgs_setup).  opts: precision, tol, max_iters, stream;
+ * v_per_cta = block_z = 0 asks kgs_autotune for the shape of the largest
+ * instance, which then applies to all; wall_norm and mass_rescale come from
+ * each kgs_problem.  Errors as kgs_setup. */
+int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_opts *opts);
+
+/* n_iters > 0: exactly n_iters outer iterations of every instance.
+ * n_iters <= 0: iterate until every instance is below opts.tol (instances
+ * retire from the work list as they converge) or max_iters iterations.
+ * iters_done[n], residuals[n] (host, may be NULL): iterations run in this
+ * call and last residual, per instance.  Returns KGS_OK, KGS_NOTCONVERGED,
+ * KGS_EDIVERGED, KGS_ETIMEOUT (a bounded wait gave up; the batch state is
+ * undefined), KGS_ECUDA. */
+int kgs_batch_iterate(kgs_batch *b, int n_iters, int *iters_done, double *residuals);
+
+/* Per-instance access: macroscopic fields to host (as kgs_moments), a new
+ * initial state (as kgs_set_initial; the instance rejoins the work list),
+ * sizes and counters (as kgs_info). */
+int kgs_batch_moments(kgs_batch *b, int i, double *out);
+int kgs_batch_set_initial(kgs_batch *b, int i, const double *macros);
+int kgs_batch_info(kgs_batch *b, int i, kgs_info_t *out);
+
+/* Summed device time (ms) of the persistent sweep launches, their number and
+ * the number of kernel launches since the last call; resets the counters. */
+int kgs_batch_profile(kgs_batch *b, double *sweep_ms, long long *sweeps, long long *kernel_launches);
+
+/* Failure-detection controls (for tests): spin_limit = polls (about 100 ns
+ * each) before a wait for an upwind block gives up (default 2e7, about 2 s);
+ * unpublished_item >= 0 makes that work item of the list never announce its
+ * completion, so the items that depend on it time out and the next
+ * kgs_batch_iterate returns KGS_ETIMEOUT; -1 restores normal operation.  No
+ * device fault is raised: the waiting thread blocks record the error and
+ * return, and the batch stays usable after kgs_batch_set_initial. */
+int kgs_batch_fault(kgs_batch *b, long long spin_limit, int unpublished_item);
+void kgs_batch_destroy(kgs_batch *b);
+
 /* ---- iteration without device allocation ----
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory themselves or through this library:

@@ -1,0 +1,422 @@
+// kgs_batch.cu -- many independent problem instances (e.g. cavities of
+// uneven sizes) advanced together: one persistent sweep launch per outer
+// iteration for all instances, the per-instance coefficient and closure
+// kernels around it, the whole iteration captured in a CUDA graph and
+// replayed.  Instances that reach the tolerance retire from the work list.
+//
+// Each instance is an ordinary context (kgs_ctx) created on the batch's
+// stream; the batch adds the persistent work list, the completion flags and
+// the graphs.  Work items are (instance, octant, velocity group, block) in
+// stage order; a CTA of the persistent kernel waits (bounded) for the three
+// upwind blocks of its item before sweeping it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kgs_ctx.h"
+
+using namespace kgs;
+
+struct kgs_batch {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;  // graphs cannot be captured on the legacy default stream
+    int n = 0;
+    std::vector<kgs_ctx *> ctx;
+    int precision = KGS_MIXED, tv = 2, bz = 32, line16 = 0, nxo_max = 1;
+    int max_iters = 1000;
+    double tol = 1e-8;
+    std::vector<char> active;
+    std::vector<int> done;  // iterations per instance since setup / set_initial
+    // persistent sweep
+    SweepArgs *d_args[2] = {nullptr, nullptr};
+    int4 *d_items = nullptr;
+    size_t items_cap = 0;
+    int n_items = 0;
+    int *d_counter = nullptr, *d_flags = nullptr, *d_flag_off = nullptr, *d_error = nullptr;
+    size_t n_flags = 0;
+    double *d_resid = nullptr;  // [2 n] + error word
+    double *h_resid = nullptr;  // pinned copy
+    int grid = 0;
+    long long spin_limit = 20000000;  // ~2 s of polling at 100 ns per poll
+    int skip_publish = -1;             // fault injection (kgs_batch_fault)
+    // graphs: [0] with the current buffers, [1] with the swapped buffers
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    bool dirty = true;
+    int next = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    double sweep_ms = 0.0;
+    long long sweeps = 0, kernel_launches = 0;
+};
+
+namespace {
+
+#define KGS_CHECK(call)                             \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return cuda_err(e_); \
+    } while (0)
+
+void swap_state(kgs_ctx *c)
+{
+    std::swap(c->mac, c->mac_new);
+    std::swap(c->rho_w, c->rho_w_new);
+}
+
+void destroy_graphs(kgs_batch *b)
+{
+    for (auto &e : b->exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+}
+
+// Work list of the active instances in stage order.
+int build_items(kgs_batch *b)
+{
+    std::vector<int4> items;
+    int max_stage = 0;
+    for (int i = 0; i < b->n; i++)
+        if (b->active[i]) max_stage = std::max(max_stage, (int)b->ctx[i]->t.stage_n.size());
+    for (int s = 0; s < max_stage; s++)
+        for (int i = 0; i < b->n; i++) {
+            if (!b->active[i]) continue;
+            const HostTables &t = b->ctx[i]->t;
+            for (int o = 0; o < 8; o++) {
+                const int ng = (t.oct_vcount[o] + t.vg_size - 1) / t.vg_size;
+                for (int vg = 0; vg < ng; vg++)
+                    for (int bzr = 0; bzr < t.nbz; bzr++)
+                        for (int byr = 0; byr < t.nby; byr++) {
+                            const int bxr = s - bzr - byr;
+                            if (bxr < 0 || bxr >= t.nbx) continue;
+                            items.push_back(
+                                make_int4(i, (o << 24) | vg, bxr | (byr << 10) | (bzr << 20), t.oct_vgbase[o] + vg));
+                        }
+            }
+        }
+    b->n_items = (int)items.size();
+    if (items.size() > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        KGS_CHECK(cudaMalloc(&b->d_items, items.size() * sizeof(int4)));
+        b->items_cap = items.size();
+    }
+    if (!items.empty())
+        KGS_CHECK(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    return KGS_OK;
+}
+
+int upload_args(kgs_batch *b, int which)
+{
+    std::vector<SweepArgs> args(b->n);
+    for (int i = 0; i < b->n; i++) args[i] = ctx_sweep_args(b->ctx[i]);
+    KGS_CHECK(cudaMemcpy(b->d_args[which], args.data(), args.size() * sizeof(SweepArgs), cudaMemcpyHostToDevice));
+    return KGS_OK;
+}
+
+// Enqueue one outer iteration of every active instance (no host sync).
+int enqueue_iteration(kgs_batch *b, int which)
+{
+    int rc;
+    cudaStream_t st = b->stream;
+    for (int i = 0; i < b->n; i++)
+        if (b->active[i] && (rc = ctx_launch_coef(b->ctx[i]))) return rc;
+    KGS_CHECK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+    KGS_CHECK(cudaMemsetAsync(b->d_flags, 0, b->n_flags * sizeof(int), st));
+    KGS_CHECK(cudaMemsetAsync(b->d_error, 0, sizeof(int), st));
+    BatchSweepArgs ba;
+    ba.inst = b->d_args[which];
+    ba.items = b->d_items;
+    ba.n_items = b->n_items;
+    ba.counter = b->d_counter;
+    ba.flags = b->d_flags;
+    ba.flag_off = b->d_flag_off;
+    ba.error = b->d_error;
+    ba.spin_limit = b->spin_limit;
+    ba.skip_publish = b->skip_publish;
+    // external records: inside a capture a plain record only orders streams
+    KGS_CHECK(cudaEventRecordWithFlags(b->ev[0], st, cudaEventRecordExternal));
+    KGS_CHECK(launch_sweep_persistent(b->precision, b->tv, b->line16, ba, b->nxo_max, b->grid, st));
+    KGS_CHECK(cudaEventRecordWithFlags(b->ev[1], st, cudaEventRecordExternal));
+    for (int i = 0; i < b->n; i++)
+        if (b->active[i] && (rc = ctx_launch_closure(b->ctx[i], b->d_resid + 2 * i))) return rc;
+    KGS_CHECK(cudaMemcpyAsync(b->h_resid, b->d_resid, (2 * b->n + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return KGS_OK;
+}
+
+// Capture the two graphs (current buffers, swapped buffers).
+int rebuild(kgs_batch *b)
+{
+    int rc;
+    destroy_graphs(b);
+    if ((rc = build_items(b))) return rc;
+    for (int which = 0; which < 2; which++) {
+        if ((rc = upload_args(b, which))) return rc;
+        cudaGraph_t g = nullptr;
+        KGS_CHECK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_iteration(b, which);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        KGS_CHECK(e);
+        e = cudaGraphInstantiate(&b->exec[which], g, 0);
+        cudaGraphDestroy(g);
+        KGS_CHECK(e);
+        for (int i = 0; i < b->n; i++) swap_state(b->ctx[i]);
+    }
+    // two swaps: every instance is back on its current buffers
+    b->next = 0;
+    b->dirty = false;
+    return KGS_OK;
+}
+
+void free_batch(kgs_batch *b)
+{
+    destroy_graphs(b);
+    for (kgs_ctx *c : b->ctx)
+        if (c) {
+            ctx_free(c);
+            delete c;
+        }
+    b->ctx.clear();
+    // d_error lives inside d_resid
+    void *bufs[] = {b->d_args[0], b->d_args[1], b->d_items, b->d_counter, b->d_flags, b->d_flag_off, b->d_resid};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (b->h_resid) cudaFreeHost(b->h_resid);
+    for (auto &e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_opts *opts)
+{
+    if (!out || n < 1 || !probs || !opts) return KGS_EINVAL;
+    *out = nullptr;
+    int vpc = opts->v_per_cta, bz = opts->block_z;
+    if (vpc == 0 && bz == 0) {
+        // shapes of the largest instance, picked by the autotuner
+        int big = 0;
+        long long best = -1;
+        for (int i = 0; i < n; i++) {
+            const long long pp = (long long)probs[i].grid.nx * probs[i].grid.ny * probs[i].grid.nz *
+                                 probs[i].vgrid.nvx * probs[i].vgrid.nvy * probs[i].vgrid.nvz;
+            if (pp > best) best = pp, big = i;
+        }
+        int rc = kgs_autotune(&probs[big], opts->precision, &vpc, &bz);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < n; i++) {
+        const kgs_problem &p = probs[i];
+        int rc = validate_problem(&p.grid, p.solid, &p.vgrid, &p.gas, &p.bc, opts->precision, p.wall_norm, vpc, bz);
+        if (rc) return rc;
+    }
+    (void)cudaGetLastError();  // launches below check their own status
+    kgs_batch *b = new (std::nothrow) kgs_batch();
+    if (!b) return KGS_ENOMEM;
+    auto fail = [&](int rc) {
+        free_batch(b);
+        delete b;
+        return rc;
+    };
+    if (cudaGetDevice(&b->dev) != cudaSuccess) return fail(KGS_ECUDA);
+    b->stream = static_cast<cudaStream_t>(opts->stream);
+    if (!b->stream) {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(KGS_ECUDA);
+        b->own_stream = true;
+    }
+    b->n = n;
+    b->precision = opts->precision;
+    b->max_iters = opts->max_iters > 0 ? opts->max_iters : 1000;
+    b->tol = opts->tol > 0.0 ? opts->tol : 1e-8;
+    b->ctx.assign(n, nullptr);
+    b->active.assign(n, 1);
+    b->done.assign(n, 0);
+    std::vector<int> flag_off(n);
+    b->line16 = 1;
+    for (int i = 0; i < n; i++) {
+        const kgs_problem &p = probs[i];
+        kgs_opts o = *opts;
+        o.stream = b->stream;
+        o.wall_norm = p.wall_norm;
+        o.mass_rescale = p.mass_rescale;
+        o.v_per_cta = vpc;
+        o.block_z = bz;
+        int rc = ctx_create(&b->ctx[i], &p.grid, p.solid, &p.vgrid, &p.gas, &p.bc, &o);
+        if (rc) return fail(rc);
+        const HostTables &t = b->ctx[i]->t;
+        b->tv = t.tv;
+        b->bz = t.bz;
+        b->nxo_max = std::max(b->nxo_max, t.nxo_max);
+        for (int q = 0; q < 8; q++)
+            if (t.oct_vcount[q] > 0 && t.oct_nx[q] != 16) b->line16 = 0;
+        flag_off[i] = (int)b->n_flags;
+        b->n_flags += (size_t)t.n_vg * t.nbx * t.nby * t.nbz;
+    }
+    // every instance must see the same shared-memory layout
+    for (int i = 0; i < n; i++) b->ctx[i]->t.nxo_max = b->nxo_max;
+    if (cudaMalloc(&b->d_args[0], n * sizeof(SweepArgs)) != cudaSuccess ||
+        cudaMalloc(&b->d_args[1], n * sizeof(SweepArgs)) != cudaSuccess ||
+        cudaMalloc(&b->d_counter, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_flags, std::max<size_t>(b->n_flags, 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_flag_off, n * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_resid, (2 * n + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&b->h_resid, (2 * n + 1) * sizeof(double)) != cudaSuccess)
+        return fail(KGS_ENOMEM);
+    // the error word shares the residual buffer so one copy brings both back
+    b->d_error = reinterpret_cast<int *>(b->d_resid + 2 * n);
+    if (cudaMemcpy(b->d_flag_off, flag_off.data(), n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_resid, 0, (2 * n + 1) * sizeof(double)) != cudaSuccess ||
+        cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess)
+        return fail(KGS_ECUDA);
+    // persistent grid: as many CTAs as fit on the device at once
+    int sms = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess) return fail(KGS_ECUDA);
+    const size_t smem = sweep_smem_bytes(b->precision, b->tv, b->nxo_max);
+    per_sm = sweep_persistent_occupancy(b->precision, b->tv, b->line16, smem);
+    if (per_sm < 1) return fail(KGS_ECUDA);
+    b->grid = sms * per_sm;
+    *out = b;
+    return KGS_OK;
+}
+
+int kgs_batch_iterate(kgs_batch *b, int n_iters, int *iters_done, double *residuals)
+{
+    if (!b) return KGS_EINVAL;
+    if (cudaSetDevice(b->dev) != cudaSuccess) return KGS_ECUDA;
+    (void)cudaGetLastError();  // launches below check their own status
+    const bool until = n_iters <= 0;
+    const int limit = until ? b->max_iters : n_iters;
+    std::vector<int> count(b->n, 0);
+    std::vector<double> last(b->n, -1.0);
+    for (int i = 0; i < b->n; i++) last[i] = b->ctx[i]->last_residual;
+    if (!until) {
+        // a fixed number of iterations runs every instance, retired or not
+        for (int i = 0; i < b->n; i++)
+            if (!b->active[i]) {
+                b->active[i] = 1;
+                b->dirty = true;
+            }
+    }
+    int rc = KGS_OK;
+    for (int k = 0; k < limit; k++) {
+        bool any = false;
+        for (int i = 0; i < b->n; i++) any |= b->active[i] != 0;
+        if (!any) break;
+        if (b->dirty && (rc = rebuild(b))) break;
+        const int which = b->next;
+        cudaError_t e = cudaGraphLaunch(b->exec[which], b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_err(e);
+            break;
+        }
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+        if (e != cudaSuccess) {
+            rc = cuda_err(e);
+            break;
+        }
+        b->sweep_ms += ms;
+        b->sweeps++;
+        const int *err = reinterpret_cast<const int *>(b->h_resid + 2 * b->n);
+        if (*err) {
+            rc = KGS_ETIMEOUT;
+            break;
+        }
+        bool bad = false, retire = false;
+        for (int i = 0; i < b->n; i++) {
+            if (!b->active[i]) continue;
+            const double r = b->h_resid[2 * i];
+            bad |= b->h_resid[2 * i + 1] != 0.0;
+            ctx_finish(b->ctx[i], r);
+            b->kernel_launches += 5;
+            count[i]++;
+            b->done[i]++;
+            last[i] = r;
+            if (until && r < b->tol) {
+                b->active[i] = 0;
+                retire = true;
+            }
+        }
+        b->kernel_launches += 1;
+        b->next = 1 - which;
+        if (retire) b->dirty = true;
+        if (bad) {
+            rc = KGS_EDIVERGED;
+            break;
+        }
+    }
+    if (rc == KGS_OK && until)
+        for (int i = 0; i < b->n; i++)
+            if (!(last[i] >= 0.0 && last[i] < b->tol)) rc = KGS_NOTCONVERGED;
+    if (iters_done)
+        for (int i = 0; i < b->n; i++) iters_done[i] = count[i];
+    if (residuals)
+        for (int i = 0; i < b->n; i++) residuals[i] = last[i];
+    return rc;
+}
+
+int kgs_batch_moments(kgs_batch *b, int i, double *out)
+{
+    if (!b || i < 0 || i >= b->n) return KGS_EINVAL;
+    return kgs_moments(b->ctx[i], out);
+}
+
+int kgs_batch_set_initial(kgs_batch *b, int i, const double *macros)
+{
+    if (!b || i < 0 || i >= b->n) return KGS_EINVAL;
+    const int rc = kgs_set_initial(b->ctx[i], macros);
+    b->active[i] = 1;
+    b->done[i] = 0;
+    b->dirty = true;  // the reference mass is a launch parameter of the graphs
+    return rc;
+}
+
+int kgs_batch_info(kgs_batch *b, int i, kgs_info_t *out)
+{
+    if (!b || i < 0 || i >= b->n) return KGS_EINVAL;
+    return kgs_info(b->ctx[i], out);
+}
+
+int kgs_batch_profile(kgs_batch *b, double *sweep_ms, long long *sweeps, long long *kernel_launches)
+{
+    if (!b) return KGS_EINVAL;
+    if (sweep_ms) *sweep_ms = b->sweep_ms;
+    if (sweeps) *sweeps = b->sweeps;
+    if (kernel_launches) *kernel_launches = b->kernel_launches;
+    b->sweep_ms = 0.0;
+    b->sweeps = 0;
+    b->kernel_launches = 0;
+    return KGS_OK;
+}
+
+int kgs_batch_fault(kgs_batch *b, long long spin_limit, int unpublished_item)
+{
+    if (!b || spin_limit < 1) return KGS_EINVAL;
+    b->spin_limit = spin_limit;
+    b->skip_publish = unpublished_item;
+    b->dirty = true;  // both are launch parameters of the graphs
+    return KGS_OK;
+}
+
+void kgs_batch_destroy(kgs_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->dev);
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    delete b;
+}
+
+}  // extern "C"

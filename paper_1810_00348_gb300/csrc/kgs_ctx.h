@@ -1,0 +1,66 @@
+// kgs_ctx.h -- the context of one problem instance and the phases of one
+// outer iteration, shared by the single-instance ABI (kgs_runtime.cu) and the
+// batched ABI (kgs_batch.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "kgs_tables.h"
+
+struct kgs_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    kgs::HostTables t;
+    int mass_rescale = 0;
+    int max_iters = 1000;
+    double tol = 1e-8;
+    double M0 = 0.0;
+    int iteration = 0;
+    double last_residual = -1.0;
+    int n_red_blocks = 0;
+    // device buffers
+    double *mac = nullptr, *mac_new = nullptr, *rho_w = nullptr, *rho_w_new = nullptr;
+    void *coef = nullptr, *vel = nullptr, *velm = nullptr, *mtab = nullptr, *FX = nullptr, *FY = nullptr,
+         *FZ = nullptr;
+    void *part = nullptr;
+    double *vel64 = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;
+    double *ddx = nullptr, *ddy = nullptr, *ddz = nullptr;
+    uint8_t *solid = nullptr, *side_flags = nullptr;
+    int8_t *wall_kind = nullptr;
+    double *wall_norm = nullptr;
+    int4 *work = nullptr;
+    int *d_vstart = nullptr, *d_vcount = nullptr, *d_vgbase = nullptr, *d_vg_oct = nullptr;
+    double *blk_mass = nullptr, *blk_res = nullptr, *scale = nullptr, *resid = nullptr;
+    int *blk_bad = nullptr;
+    double *h_resid = nullptr;  // pinned
+    size_t device_bytes = 0;
+    std::vector<void *> allocs;
+    // profiling
+    int profiling = 0;
+    std::vector<cudaEvent_t> ev;
+    double sweep_ms = 0.0;
+    long long sweep_launches = 0, kernel_launches = 0;
+};
+
+
+namespace kgs {
+
+int cuda_err(cudaError_t e);
+
+// Build a context on the current device and `stream` (validated inputs).
+int ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
+               const kgs_bc *bc, const kgs_opts *opts);
+void ctx_free(kgs_ctx *c);
+SweepArgs ctx_sweep_args(const kgs_ctx *c);
+// Phases of one outer iteration (asynchronous on the context's stream).
+int ctx_launch_coef(kgs_ctx *c);
+int ctx_launch_stages(kgs_ctx *c);
+// Closure into the new buffers; the residual and divergence flag go to
+// resid_dev[0..1] (device).
+int ctx_launch_closure(kgs_ctx *c, double *resid_dev);
+// After the iteration's work has completed: swap the state buffers.
+void ctx_finish(kgs_ctx *c, double residual);
+
+}  // namespace kgs

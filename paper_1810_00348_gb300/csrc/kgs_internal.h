@@ -76,6 +76,27 @@ struct SweepArgs {
     int line16;                   // every octant has x-lines of 16 nodes (specialised moment loop)
 };
 
+// Persistent sweep over the work items of many instances (one launch per
+// outer iteration): item = (instance, octant << 24 | velocity group of the
+// octant, reflected block coordinates bx | by << 10 | bz << 20, global
+// velocity-group index within the instance), list ordered by stage.
+struct BatchSweepArgs {
+    const SweepArgs *inst;        // [n_inst] per-instance arguments (device)
+    const int4 *items;
+    int n_items;
+    int *counter;                 // claim counter, zero at launch
+    int *flags;                   // completion flags, zero at launch
+    const int *flag_off;          // [n_inst] first flag of each instance
+    int *error;                   // set to 1 when a bounded wait gives up
+    long long spin_limit;         // polls before a wait gives up
+    int skip_publish;             // fault injection: this item never sets its flag (-1: none)
+};
+
+cudaError_t launch_sweep_persistent(int precision, int tv, int line16, const BatchSweepArgs &b, int nxo_max,
+                                    int grid, cudaStream_t s);
+// Resident CTAs per SM of the persistent kernel (also sets its shared-memory limit).
+int sweep_persistent_occupancy(int precision, int tv, int line16, size_t smem);
+
 // Sweep launch (one wavefront stage).  precision: 0 FP64, 1 FP32.
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s);
 size_t sweep_smem_bytes(int precision, int tv, int nxo_max);

@@ -105,6 +105,7 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return KGS_ECUDA;
+    (void)cudaGetLastError();  // launches below check their own status
     void *base = nullptr;
     if ((rc = scratch_address(dev, &base))) return rc;
     unsigned char *b = static_cast<unsigned char *>(base);

@@ -17,7 +17,7 @@
 #include <new>
 #include <vector>
 
-#include "kgs_tables.h"
+#include "kgs_ctx.h"
 
 using namespace kgs;
 
@@ -25,49 +25,14 @@ namespace {
 constexpr uint32_t CKPT_MAGIC = 0x4b475331u;  // "KGS1"
 }
 
-struct kgs_ctx {
-    int dev = 0;
-    cudaStream_t stream = nullptr;
-    HostTables t;
-    int mass_rescale = 0;
-    int max_iters = 1000;
-    double tol = 1e-8;
-    double M0 = 0.0;
-    int iteration = 0;
-    double last_residual = -1.0;
-    int n_red_blocks = 0;
-    // device buffers
-    double *mac = nullptr, *mac_new = nullptr, *rho_w = nullptr, *rho_w_new = nullptr;
-    void *coef = nullptr, *vel = nullptr, *velm = nullptr, *mtab = nullptr, *FX = nullptr, *FY = nullptr,
-         *FZ = nullptr;
-    void *part = nullptr;
-    double *vel64 = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;
-    double *ddx = nullptr, *ddy = nullptr, *ddz = nullptr;
-    uint8_t *solid = nullptr, *side_flags = nullptr;
-    int8_t *wall_kind = nullptr;
-    double *wall_norm = nullptr;
-    int4 *work = nullptr;
-    int *d_vstart = nullptr, *d_vcount = nullptr, *d_vgbase = nullptr, *d_vg_oct = nullptr;
-    double *blk_mass = nullptr, *blk_res = nullptr, *scale = nullptr, *resid = nullptr;
-    int *blk_bad = nullptr;
-    double *h_resid = nullptr;  // pinned
-    size_t device_bytes = 0;
-    std::vector<void *> allocs;
-    // profiling
-    int profiling = 0;
-    std::vector<cudaEvent_t> ev;
-    double sweep_ms = 0.0;
-    long long sweep_launches = 0, kernel_launches = 0;
-};
-
-namespace {
-
-int cuda_err(cudaError_t e)
+int kgs::cuda_err(cudaError_t e)
 {
     if (e == cudaSuccess) return KGS_OK;
     if (e == cudaErrorMemoryAllocation) return KGS_ENOMEM;
     return KGS_ECUDA;
 }
+
+namespace {
 
 #define KGS_CHECK(call)                             \
     do {                                            \
@@ -166,10 +131,12 @@ int initial_state(kgs_ctx *c, const double *macros)
     return KGS_OK;
 }
 
-SweepArgs sweep_args(const kgs_ctx *c)
+}  // namespace
+
+SweepArgs kgs::ctx_sweep_args(const kgs_ctx *c)
 {
     const HostTables &t = c->t;
-    SweepArgs a;
+    SweepArgs a{};
     a.nx = t.nx;
     a.ny = t.ny;
     a.nz = t.nz;
@@ -203,13 +170,20 @@ SweepArgs sweep_args(const kgs_ctx *c)
     return a;
 }
 
-int run_iteration(kgs_ctx *c, double *residual, int *bad)
+int kgs::ctx_launch_coef(kgs_ctx *c)
+{
+    const HostTables &t = c->t;
+    KGS_CHECK(launch_coef(t.precision, c->mac, c->solid, c->side_flags, c->rdx, c->rdy, c->rdz, t.nx, t.ny, t.nz,
+                          t.mu_ref, t.omega, t.Pr, c->coef, c->stream));
+    c->kernel_launches += 1;
+    return KGS_OK;
+}
+
+int kgs::ctx_launch_stages(kgs_ctx *c)
 {
     const HostTables &t = c->t;
     cudaStream_t st = c->stream;
-    KGS_CHECK(launch_coef(t.precision, c->mac, c->solid, c->side_flags, c->rdx, c->rdy, c->rdz, t.nx, t.ny, t.nz,
-                          t.mu_ref, t.omega, t.Pr, c->coef, st));
-    SweepArgs a = sweep_args(c);
+    SweepArgs a = ctx_sweep_args(c);
     const int ns = (int)t.stage_n.size();
     for (int s = 0; s < ns; s++) {
         a.work = c->work + t.stage_off[s];
@@ -217,6 +191,15 @@ int run_iteration(kgs_ctx *c, double *residual, int *bad)
         KGS_CHECK(launch_sweep(t.precision, t.tv, a, t.stage_n[s], t.max_vg, st));
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[2 * s + 1], st));
     }
+    c->kernel_launches += ns;
+    c->sweep_launches += ns;
+    return KGS_OK;
+}
+
+int kgs::ctx_launch_closure(kgs_ctx *c, double *resid_dev)
+{
+    const HostTables &t = c->t;
+    cudaStream_t st = c->stream;
     CloseArgs ca;
     ca.nx = t.nx;
     ca.ny = t.ny;
@@ -241,24 +224,38 @@ int run_iteration(kgs_ctx *c, double *residual, int *bad)
     KGS_CHECK(launch_finalize_mass(c->blk_mass, c->n_red_blocks, c->M0, c->mass_rescale, c->scale, st));
     KGS_CHECK(launch_scale_residual(c->mac_new, c->rho_w_new, c->mac, c->solid, t.ncell, c->scale, c->blk_res,
                                     c->blk_bad, c->n_red_blocks, st));
-    KGS_CHECK(launch_finalize_residual(c->blk_res, c->blk_bad, c->n_red_blocks, c->resid, st));
-    KGS_CHECK(cudaMemcpyAsync(c->h_resid, c->resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    KGS_CHECK(cudaStreamSynchronize(st));
-    c->kernel_launches += 5 + ns;
-    c->sweep_launches += ns;
+    KGS_CHECK(launch_finalize_residual(c->blk_res, c->blk_bad, c->n_red_blocks, resid_dev, st));
+    c->kernel_launches += 4;
+    return KGS_OK;
+}
+
+void kgs::ctx_finish(kgs_ctx *c, double residual)
+{
+    std::swap(c->mac, c->mac_new);
+    std::swap(c->rho_w, c->rho_w_new);
+    c->iteration++;
+    c->last_residual = residual;
+}
+
+namespace {
+
+int run_iteration(kgs_ctx *c, double *residual, int *bad)
+{
+    int rc;
+    if ((rc = ctx_launch_coef(c)) || (rc = ctx_launch_stages(c)) || (rc = ctx_launch_closure(c, c->resid)))
+        return rc;
+    KGS_CHECK(cudaMemcpyAsync(c->h_resid, c->resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    KGS_CHECK(cudaStreamSynchronize(c->stream));
     if (c->profiling) {
-        for (int s = 0; s < ns; s++) {
+        for (size_t s = 0; s < c->t.stage_n.size(); s++) {
             float ms = 0.f;
             KGS_CHECK(cudaEventElapsedTime(&ms, c->ev[2 * s], c->ev[2 * s + 1]));
             c->sweep_ms += ms;
         }
     }
-    std::swap(c->mac, c->mac_new);
-    std::swap(c->rho_w, c->rho_w_new);
-    c->iteration++;
     *residual = c->h_resid[0];
     *bad = c->h_resid[1] != 0.0;
-    c->last_residual = *residual;
+    ctx_finish(c, *residual);
     return KGS_OK;
 }
 
@@ -289,6 +286,18 @@ int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const k
     int rc = validate_problem(grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta,
                               opts->block_z);
     if (rc) return rc;
+    (void)cudaGetLastError();  // launches below check their own status
+    return ctx_create(out, grid, solid, vg, gas, bc, opts);
+}
+
+}  // extern "C"
+
+void kgs::ctx_free(kgs_ctx *c) { free_all(c); }
+
+int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
+                    const kgs_bc *bc, const kgs_opts *opts)
+{
+    int rc = KGS_OK;
     kgs_ctx *c = new (std::nothrow) kgs_ctx();
     if (!c) return KGS_ENOMEM;
     auto fail = [&](int code) {
@@ -346,10 +355,13 @@ int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const k
     return KGS_OK;
 }
 
+extern "C" {
+
 int kgs_set_initial(kgs_ctx *c, const double *macros)
 {
     if (!c) return KGS_EINVAL;
     if (cudaSetDevice(c->dev) != cudaSuccess) return KGS_ECUDA;
+    (void)cudaGetLastError();  // launches below check their own status
     return initial_state(c, macros);
 }
 
@@ -357,6 +369,7 @@ int kgs_iterate(kgs_ctx *c, int n_iters, int *done, double *residual)
 {
     if (!c) return KGS_EINVAL;
     if (cudaSetDevice(c->dev) != cudaSuccess) return KGS_ECUDA;
+    (void)cudaGetLastError();  // launches below check their own status
     int count = 0, bad = 0, rc = KGS_OK;
     double r = c->last_residual;
     const bool until = n_iters <= 0;

@@ -167,13 +167,26 @@ __device__ __forceinline__ float2 pair_add(float s0, float c0, float s1, float c
     return make_float2(hi, -lo);
 }
 
-template <typename Real, int TV, int LINE>
-__global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
+// Face-plane load: in the persistent kernel the value may have been written
+// by another CTA during the same launch, so it bypasses L1 (the acquire of the
+// upwind block's completion flag orders it after that CTA's stores).
+template <bool COHERENT, typename Real>
+__device__ __forceinline__ Real ld_face(const Real *p)
+{
+    if constexpr (COHERENT)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+// One work item: block w = (octant, reflected block coordinates) and
+// velocity group vgy of that octant.  Called by every thread of the CTA.
+template <typename Real, int TV, int LINE, bool COHERENT>
+__device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, const int vgy, unsigned char *smem)
 {
     using L = SmemLayout<Real, TV>;
     constexpr int VG = L::VG;
     constexpr int CS = L::CS;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int nxm = a.nxo_max;
     Real *slice = reinterpret_cast<Real *>(smem);
     Real *cs = reinterpret_cast<Real *>(smem + L::slice_bytes);
@@ -185,14 +198,13 @@ __global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
     Real *cxl = cxh + align16(sizeof(Real) * SLICE * cxs) / sizeof(Real);                    // [SLICE][cxs]
 
     const int t = threadIdx.x;
-    const int4 w = a.work[blockIdx.x];
     const int o = w.x;
     const int vcount = a.oct_vcount[o];
-    const int v0 = blockIdx.y * VG;
+    const int v0 = vgy * VG;
     if (v0 >= vcount) return;
     const int nvg = min(VG, vcount - v0);
     const int gvbase = a.oct_vstart[o] + v0;
-    const int vgid = a.oct_vgbase[o] + blockIdx.y;
+    const int vgid = a.oct_vgbase[o] + vgy;
     const int nxo = a.oct_nx[o];
 
     // Octant bit d set: xi_d >= 0, sweep towards +d.
@@ -281,7 +293,7 @@ __global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
 #pragma unroll
         for (int m = 0; m < TV; m++) {
             if (!ok[m]) continue;
-            const Real v = zfirst ? rw * mgz[m] : FZp[((size_t)y * nx + x) * Nv + gv[m]];
+            const Real v = zfirst ? rw * mgz[m] : ld_face<COHERENT>(FZp + ((size_t)y * nx + x) * Nv + gv[m]);
             slice[SL(li, lj) + t + m * NT] = v;
         }
     }
@@ -308,7 +320,8 @@ __global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
             const Real rw = xfirst ? wall_rho(sidex, CELL(x, y, z)) : Real(0);
 #pragma unroll
             for (int m = 0; m < TV; m++)
-                phx[lj2][m] = xfirst ? rw * mgx[m] : (ok[m] ? FXp[((size_t)z * ny + y) * Nv + gv[m]] : Real(0));
+                phx[lj2][m] = xfirst ? rw * mgx[m]
+                                     : (ok[m] ? ld_face<COHERENT>(FXp + ((size_t)z * ny + y) * Nv + gv[m]) : Real(0));
         }
 #pragma unroll
         for (int li2 = 0; li2 < BX; li2++) {
@@ -317,7 +330,8 @@ __global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
             const Real rw = yfirst ? wall_rho(sidey, CELL(x, y, z)) : Real(0);
 #pragma unroll
             for (int m = 0; m < TV; m++)
-                phy[li2][m] = yfirst ? rw * mgy[m] : (ok[m] ? FYp[((size_t)z * nx + x) * Nv + gv[m]] : Real(0));
+                phy[li2][m] = yfirst ? rw * mgy[m]
+                                     : (ok[m] ? ld_face<COHERENT>(FYp + ((size_t)z * nx + x) * Nv + gv[m]) : Real(0));
         }
     };
     prefetch(0);
@@ -574,6 +588,85 @@ __global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
     }
 }
 
+// One wavefront stage: CTA (x, y) = (work item x of the stage, velocity group y).
+template <typename Real, int TV, int LINE>
+__global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    sweep_item<Real, TV, LINE, false>(a, a.work[blockIdx.x], blockIdx.y, smem);
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait for a completion flag: true once it is set, false after
+// `limit` polls (the caller then records an error and returns).
+__device__ bool wait_flag(const int *p, long long limit)
+{
+    for (long long i = 0; i < limit; i++) {
+        if (ld_acquire(p) != 0) return true;
+        __nanosleep(100);
+    }
+    return false;
+}
+
+// Persistent sweep over the items of many problem instances.  Items are
+// claimed in list order (stage-major), so every item's upwind dependencies
+// were claimed earlier by CTAs that are running: the waits always end unless
+// an error stopped a producer, and then they end at the poll limit.
+template <typename Real, int TV, int LINE>
+__global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSweepArgs b)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SweepArgs sa;
+    __shared__ int s_item, s_go;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(b.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= b.n_items) break;
+        const int4 item = b.items[it];
+        const int inst = item.x, o = item.y >> 24, vg = item.y & 0xffffff;
+        const int bxr = item.z & 1023, byr = (item.z >> 10) & 1023, bzr = (item.z >> 20) & 1023;
+        // copy the instance's arguments to shared memory (words of the struct)
+        {
+            const int *src = reinterpret_cast<const int *>(b.inst + inst);
+            int *dst = reinterpret_cast<int *>(&sa);
+            for (int q = threadIdx.x; q < (int)(sizeof(SweepArgs) / sizeof(int)); q += NT) dst[q] = src[q];
+        }
+        int *fl = b.flags + b.flag_off[inst];
+        if (threadIdx.x == 0) {
+            const SweepArgs &a = b.inst[inst];
+            const int vgg = item.w;  // global velocity-group index within the instance
+            auto fidx = [&](int x, int y, int z) { return ((vgg * a.nbz + z) * a.nby + y) * a.nbx + x; };
+            bool ok = *b.error == 0;
+            if (ok && bxr > 0) ok = wait_flag(fl + fidx(bxr - 1, byr, bzr), b.spin_limit);
+            if (ok && byr > 0) ok = wait_flag(fl + fidx(bxr, byr - 1, bzr), b.spin_limit);
+            if (ok && bzr > 0) ok = wait_flag(fl + fidx(bxr, byr, bzr - 1), b.spin_limit);
+            if (!ok) atomicExch(b.error, 1);
+            s_go = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        sweep_item<Real, TV, LINE, true>(sa, make_int4(o, bxr, byr, bzr), vg, smem);
+        __syncthreads();
+        if (threadIdx.x == 0 && it != b.skip_publish) {
+            __threadfence();
+            const int vgg = item.w;
+            st_release(fl + ((vgg * sa.nbz + bzr) * sa.nby + byr) * sa.nbx + bxr, 1);
+        }
+    }
+}
+
 template <typename Real, int TV, int LINE>
 cudaError_t launch_t(const SweepArgs &a, int n_items, int max_vg, cudaStream_t s)
 {
@@ -598,7 +691,59 @@ cudaError_t launch_line(const SweepArgs &a, int n_items, int max_vg, cudaStream_
     return launch_t<Real, TV, 0>(a, n_items, max_vg, s);
 }
 
+template <typename Real, int TV, int LINE>
+cudaError_t launch_persistent_t(const BatchSweepArgs &b, int nxo_max, int grid, cudaStream_t s)
+{
+    using L = SmemLayout<Real, TV>;
+    static size_t configured = 0;
+    const size_t bytes = L::total(nxo_max);
+    if (bytes > configured) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        configured = bytes;
+    }
+    sweep_persistent_kernel<Real, TV, LINE><<<grid, NT, bytes, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename Real, int TV, int LINE>
+int occupancy_t(size_t smem)
+{
+    int n = 0;
+    if (cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_persistent_kernel<Real, TV, LINE>, NT, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
 }  // namespace
+
+int sweep_persistent_occupancy(int precision, int tv, int line16, size_t smem)
+{
+    if (precision == 0) return line16 ? occupancy_t<double, 1, 16>(smem) : occupancy_t<double, 1, 0>(smem);
+    if (tv == 2) return line16 ? occupancy_t<float, 2, 16>(smem) : occupancy_t<float, 2, 0>(smem);
+    return line16 ? occupancy_t<float, 1, 16>(smem) : occupancy_t<float, 1, 0>(smem);
+}
+
+cudaError_t launch_sweep_persistent(int precision, int tv, int line16, const BatchSweepArgs &b, int nxo_max, int grid,
+                                    cudaStream_t s)
+{
+    if (b.n_items == 0) return cudaSuccess;
+    if (precision == 0)
+        return line16 ? launch_persistent_t<double, 1, 16>(b, nxo_max, grid, s)
+                      : launch_persistent_t<double, 1, 0>(b, nxo_max, grid, s);
+    if (tv == 2)
+        return line16 ? launch_persistent_t<float, 2, 16>(b, nxo_max, grid, s)
+                      : launch_persistent_t<float, 2, 0>(b, nxo_max, grid, s);
+    return line16 ? launch_persistent_t<float, 1, 16>(b, nxo_max, grid, s)
+                  : launch_persistent_t<float, 1, 0>(b, nxo_max, grid, s);
+}
 
 size_t sweep_smem_bytes(int precision, int tv, int nxo_max)
 {

@@ -306,3 +306,112 @@ def kgs_iterate_noalloc(prob, macros_in, rho_w_in, macros_out, rho_w_out, M0=0.0
                                     ctypes.c_void_p(stream) if stream else None)
     _check(rc, "kgs_iterate_noalloc", allow=(KGS_EDIVERGED,))
     return rc, res.value
+
+
+# ---- batches ----
+
+class KgsProblem(ctypes.Structure):
+    _fields_ = [("grid", KgsGrid), ("solid", ctypes.POINTER(ctypes.c_uint8)), ("vgrid", KgsVgrid),
+                ("gas", KgsGas), ("bc", KgsBc), ("wall_norm", ctypes.c_int), ("mass_rescale", ctypes.c_int)]
+
+
+SIGNATURES.update({
+    "kgs_autotune": (ctypes.c_int, [ctypes.POINTER(KgsProblem), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]),
+    "kgs_batch_setup": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(KgsProblem),
+                                       ctypes.POINTER(KgsOpts)]),
+    "kgs_batch_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]),
+    "kgs_batch_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
+    "kgs_batch_set_initial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _dp]),
+    "kgs_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(KgsInfo)]),
+    "kgs_batch_profile": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_longlong)]),
+    "kgs_batch_fault": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]),
+    "kgs_batch_destroy": (None, [ctypes.c_void_p]),
+})
+
+
+def _problem(prob, keep):
+    g, v, gas, bc, solid_p = _problem_structs(prob, keep)
+    return KgsProblem(g, solid_p, v, gas, bc, int(prob.wall_mode), int(prob.mass_rescale))
+
+
+def kgs_autotune(prob, precision=KGS_MIXED):
+    """Returns (v_per_cta, block_z) chosen by timing on the current device."""
+    keep = []
+    p = _problem(prob, keep)
+    vpc, bz = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().kgs_autotune(ctypes.byref(p), int(precision), ctypes.byref(vpc), ctypes.byref(bz)), "kgs_autotune")
+    return vpc.value, bz.value
+
+
+class Batch:
+    """Handle of one kgs_batch."""
+
+    def __init__(self, handle, probs):
+        self.handle = handle
+        self.probs = probs
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            kgs_batch_destroy(self)
+
+
+def kgs_batch_setup(probs, precision=KGS_MIXED, max_iters=1000, tol=1e-8, v_per_cta=0, block_z=0, stream=None):
+    keep = []
+    arr = (KgsProblem * len(probs))(*[_problem(p, keep) for p in probs])
+    opts = KgsOpts(precision, 0, 0, max_iters, tol, v_per_cta, block_z, ctypes.c_void_p(stream) if stream else None)
+    h = ctypes.c_void_p()
+    _check(load().kgs_batch_setup(ctypes.byref(h), len(probs), arr, ctypes.byref(opts)), "kgs_batch_setup")
+    return Batch(h, probs)
+
+
+def kgs_batch_iterate(b, n_iters=1):
+    """Returns (rc, iterations per instance, residual per instance); the
+    status codes KGS_NOTCONVERGED, KGS_EDIVERGED and KGS_ETIMEOUT are
+    returned, other errors raise."""
+    n = len(b.probs)
+    done = (ctypes.c_int * n)()
+    res = (ctypes.c_double * n)()
+    rc = load().kgs_batch_iterate(b.handle, int(n_iters), done, res)
+    _check(rc, "kgs_batch_iterate", allow=(KGS_NOTCONVERGED, KGS_EDIVERGED, KGS_ETIMEOUT))
+    return rc, list(done), list(res)
+
+
+def kgs_batch_moments(b, i):
+    p = b.probs[i]
+    out = np.empty(8 * p.ncell)
+    _check(load().kgs_batch_moments(b.handle, int(i), out.ctypes.data_as(_dp)), "kgs_batch_moments")
+    return out.reshape(8, p.nz, p.ny, p.nx)
+
+
+def kgs_batch_set_initial(b, i, macros=None):
+    if macros is None:
+        return _check(load().kgs_batch_set_initial(b.handle, int(i), _dp()), "kgs_batch_set_initial")
+    m = _arr(macros).reshape(-1)
+    return _check(load().kgs_batch_set_initial(b.handle, int(i), m.ctypes.data_as(_dp)), "kgs_batch_set_initial")
+
+
+def kgs_batch_info(b, i):
+    info = KgsInfo()
+    _check(load().kgs_batch_info(b.handle, int(i), ctypes.byref(info)), "kgs_batch_info")
+    return {name: getattr(info, name) for name, _ in KgsInfo._fields_}
+
+
+def kgs_batch_profile(b):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    kl = ctypes.c_longlong(0)
+    _check(load().kgs_batch_profile(b.handle, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(kl)),
+           "kgs_batch_profile")
+    return ms.value, n.value, kl.value
+
+
+def kgs_batch_fault(b, spin_limit=20000000, unpublished_item=-1):
+    return _check(load().kgs_batch_fault(b.handle, int(spin_limit), int(unpublished_item)), "kgs_batch_fault")
+
+
+def kgs_batch_destroy(b):
+    if b.handle:
+        load().kgs_batch_destroy(b.handle)
+        b.handle = None
