@@ -77,35 +77,79 @@ __device__ void block_sum(double (&v)[NV], double *blk)
         for (int q = 0; q < NV; q++) blk[(size_t)blockIdx.x * NV + q] = sh[q][0];
 }
 
+// Float-float accumulator: the running sum is hi + lo with |lo| <= ulp(hi)/2
+// up to the rounding of lo itself; add(x, y) adds x - y.  hi is updated by
+// Knuth's two-sum, whose rounding error is exact and goes to lo.
+struct FFSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x, float y)
+    {
+        const float t = hi + x;
+        const float bp = t - hi;
+        const float err = (hi - (t - bp)) + (x - bp);
+        hi = t;
+        lo += err - y;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Closure of one outer iteration for CLOSE_CELLS cells per block: thread
+// (slot q, cell) sums partial q of its cell over all velocity groups in group
+// order (16 threads per cell keep many loads in flight), then one thread per
+// cell turns the sums into the macroscopic fields and wall densities.
 template <typename Real>
-__global__ void __launch_bounds__(RED_THREADS) close_kernel(const CloseArgs a)
+__global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseArgs a)
 {
+    constexpr int NS = 13 + 6;  // 13 sums about U^n, incoming flux per side
+    __shared__ double sS[CLOSE_CELLS][NS];
     const size_t ncell = a.ncell;
-    const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double mass[1] = {0.0};
-    if (c < ncell && !(a.solid && a.solid[c])) {
-        double S[13];
-        double F[6] = {0, 0, 0, 0, 0, 0};
-        for (int q = 0; q < 13; q++) S[q] = 0.0;
-        for (int g = 0; g < a.n_vg; g++) {
-            double v[NPART];
-            if (sizeof(Real) == 8) {
-                const double *pp = static_cast<const double *>(a.part) + (size_t)g * NPART * ncell + c;
-                for (int q = 0; q < NPART; q++) v[q] = pp[(size_t)q * ncell];
-            } else {
-                const float2 *pp = static_cast<const float2 *>(a.part) + (size_t)g * NPART * ncell + c;
-                for (int q = 0; q < NPART; q++) {
-                    const float2 e = pp[(size_t)q * ncell];
-                    v[q] = (double)e.x - (double)e.y;
-                }
+    const int cl = threadIdx.x % CLOSE_CELLS, q = threadIdx.x / CLOSE_CELLS;
+    const size_t c = (size_t)blockIdx.x * CLOSE_CELLS + cl;
+    const bool live = c < ncell && !(a.solid && a.solid[c]);
+    if (live) {
+        const int axis = q - P_FX;  // flux slots: incoming flux along x, y, z
+        double sum, f_minus, f_plus;
+        if (sizeof(Real) == 8) {
+            sum = f_minus = f_plus = 0.0;
+            const double *pp = static_cast<const double *>(a.part) + (size_t)q * ncell + c;
+#pragma unroll 4
+            for (int g = 0; g < a.n_vg; g++) {
+                const double v = pp[(size_t)g * NPART * ncell];
+                if (q < P_FX)
+                    sum += v;
+                else if ((a.vg_oct[g] >> axis) & 1)  // the wall ahead of the group's octant
+                    f_plus += v;
+                else
+                    f_minus += v;
             }
-            for (int q = 0; q < 13; q++) S[q] += v[q];
-            const int o = a.vg_oct[g];
-            // incoming flux onto the wall ahead of the octant along each axis
-            F[(o & 1) ? 1 : 0] += v[P_FX];
-            F[(o & 2) ? 3 : 2] += v[P_FY];
-            F[(o & 4) ? 5 : 4] += v[P_FZ];
+        } else {
+            // FP32 partials are compensated pairs (value = x - y); they are
+            // summed as float-float numbers (hi + lo, hi updated by an error-
+            // free two-sum) on the FP32 pipe and widened once at the end
+            FFSum acc[2];
+            const float2 *pp = static_cast<const float2 *>(a.part) + (size_t)q * ncell + c;
+#pragma unroll 4
+            for (int g = 0; g < a.n_vg; g++) {
+                const float2 e = pp[(size_t)g * NPART * ncell];
+                const int side = q < P_FX ? 0 : ((a.vg_oct[g] >> axis) & 1);
+                acc[side].add(e.x, e.y);
+            }
+            sum = f_minus = acc[0].value();
+            f_plus = acc[1].value();
         }
+        if (q < P_FX) {
+            sS[cl][q] = sum;
+        } else {
+            sS[cl][13 + 2 * axis] = f_minus;
+            sS[cl][13 + 2 * axis + 1] = f_plus;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= CLOSE_CELLS) return;
+    double mass = 0.0;
+    if (live) {
+        const double *S = sS[cl];
+        const double *F = sS[cl] + 13;
         const Real *cf = static_cast<const Real *>(a.coef) + c * NCOEF;
         // The sums were taken about the lagged velocity U^n as stored in the
         // sweep precision; shift exactly to U^{n+1} = U^n + delta.
@@ -124,11 +168,11 @@ __global__ void __launch_bounds__(RED_THREADS) close_kernel(const CloseArgs a)
         // rho E = rho |U|^2/2 + (3/2) rho R T (Section 2.1)
         const double trP = trS2 - rho * d2;
         const double T = trP / (3.0 * rho * R_GAS);
-        double q[3];
+        double qf[3];
         for (int i = 0; i < 3; i++) {
             // q_i = 1/2 sum w f (c'-delta)_i |c'-delta|^2 expanded in the sums about U^n
             const double S2d = S2[i][0] * d[0] + S2[i][1] * d[1] + S2[i][2] * d[2];
-            q[i] = 0.5 * (S3[i] - 2.0 * S2d - d[i] * trS2 + 2.0 * d[i] * dS1 + d2 * S1[i] - rho * d2 * d[i]);
+            qf[i] = 0.5 * (S3[i] - 2.0 * S2d - d[i] * trS2 + 2.0 * d[i] * dS1 + d2 * S1[i] - rho * d2 * d[i]);
         }
         double *mn = a.mac_new;
         mn[c] = rho;
@@ -136,29 +180,42 @@ __global__ void __launch_bounds__(RED_THREADS) close_kernel(const CloseArgs a)
         mn[2 * ncell + c] = Uc[1] + d[1];
         mn[3 * ncell + c] = Uc[2] + d[2];
         mn[4 * ncell + c] = T;
-        mn[5 * ncell + c] = q[0];
-        mn[6 * ncell + c] = q[1];
-        mn[7 * ncell + c] = q[2];
+        mn[5 * ncell + c] = qf[0];
+        mn[6 * ncell + c] = qf[1];
+        mn[7 * ncell + c] = qf[2];
         for (int s = 0; s < 6; s++) {
             const int kind = a.wall_kind[s * ncell + c];
             a.rho_w_new[s * ncell + c] = kind >= 0 ? F[s] * a.wall_norm[kind * 6 + s] : 0.0;
         }
         const int i = (int)(c % a.nx), j = (int)((c / a.nx) % a.ny), k = (int)(c / ((size_t)a.nx * a.ny));
-        mass[0] = rho * a.dx[i] * a.dy[j] * a.dz[k];
+        mass = rho * a.dx[i] * a.dy[j] * a.dz[k];
     } else if (c < ncell) {
-        for (int q = 0; q < 8; q++) a.mac_new[q * ncell + c] = 0.0;
+        for (int v = 0; v < 8; v++) a.mac_new[v * ncell + c] = 0.0;
         for (int s = 0; s < 6; s++) a.rho_w_new[s * ncell + c] = 0.0;
     }
-    block_sum<1>(mass, a.blk_mass);
+    // fixed-order sum of the block's cell masses (lanes 0..15)
+    for (int off = CLOSE_CELLS / 2; off > 0; off >>= 1) mass += __shfl_down_sync(0xffffu, mass, off, CLOSE_CELLS);
+    if (threadIdx.x == 0) a.blk_mass[blockIdx.x] = mass;
 }
 
-__global__ void finalize_mass_kernel(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale)
+// Total mass (fixed order: strided per-thread sums, then a tree) and the
+// Section 3.4 rescale factor.
+__global__ void __launch_bounds__(RED_THREADS)
+    finalize_mass_kernel(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sh[RED_THREADS];
     double M = 0.0;
-    for (int b = 0; b < n_blocks; b++) M += blk_mass[b];
-    scale[0] = rescale ? M0 / M : 1.0;
-    scale[1] = M;
+    for (int b = threadIdx.x; b < n_blocks; b += RED_THREADS) M += blk_mass[b];
+    sh[threadIdx.x] = M;
+    __syncthreads();
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        scale[0] = rescale ? M0 / sh[0] : 1.0;
+        scale[1] = sh[0];
+    }
 }
 
 __global__ void __launch_bounds__(RED_THREADS)
@@ -205,18 +262,35 @@ __global__ void __launch_bounds__(RED_THREADS)
     if (threadIdx.x == 0) blk_bad[blockIdx.x] = any_bad;
 }
 
-__global__ void finalize_residual_kernel(const double *blk_res, const int *blk_bad, int n_blocks, double *out)
+__global__ void __launch_bounds__(RED_THREADS)
+    finalize_residual_kernel(const double *blk_res, const int *blk_bad, int n_blocks, double *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double dn[5] = {0, 0, 0, 0, 0}, nn[5] = {0, 0, 0, 0, 0};
+    // fixed order: strided per-thread sums over the blocks, then a tree
+    double v[10];
+    for (int t = 0; t < 10; t++) v[t] = 0.0;
     int bad = 0;
-    for (int b = 0; b < n_blocks; b++) {
-        for (int t = 0; t < 5; t++) {
-            dn[t] += blk_res[(size_t)b * 10 + t];
-            nn[t] += blk_res[(size_t)b * 10 + 5 + t];
-        }
+    for (int b = threadIdx.x; b < n_blocks; b += RED_THREADS) {
+        for (int t = 0; t < 10; t++) v[t] += blk_res[(size_t)b * 10 + t];
         bad |= blk_bad[b];
     }
+    __shared__ double sh[10][RED_THREADS];
+    __shared__ int any_bad;
+    if (threadIdx.x == 0) any_bad = 0;
+    for (int t = 0; t < 10; t++) sh[t][threadIdx.x] = v[t];
+    __syncthreads();
+    if (bad) any_bad = 1;
+    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int t = 0; t < 10; t++) sh[t][threadIdx.x] += sh[t][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double dn[5], nn[5];
+    for (int t = 0; t < 5; t++) {
+        dn[t] = sh[t][0];
+        nn[t] = sh[5 + t][0];
+    }
+    bad = any_bad;
     // Section 4.1 reading: largest relative L2 change over rho, rho U, rho E;
     // denominators floored at 1e-8 ||rho||_2.
     double res = 0.0;
@@ -231,18 +305,20 @@ __global__ void finalize_residual_kernel(const double *blk_res, const int *blk_b
     out[1] = bad ? 1.0 : 0.0;
 }
 
-// rho_w^0 from the flux of f^{S,0}: one thread per (side, cell) wall face.
-__global__ void wall_flux_init_kernel(const double *mac, const int8_t *wall_kind, const double *wall_norm,
-                                      const double *vel64, int Nv, size_t ncell, double R, double Pr,
-                                      double *rho_w)
+// rho_w^0 from the flux of f^{S,0}: one warp per (side, cell) face; the
+// lanes split the velocities and the warp sums in a fixed order.
+__global__ void __launch_bounds__(128) wall_flux_init_kernel(const double *mac, const int8_t *wall_kind,
+                                                             const double *wall_norm, const double *vel64, int Nv,
+                                                             size_t ncell, double R, double Pr, double *rho_w)
 {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t idx = (size_t)blockIdx.x * 4 + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
     if (idx >= 6 * ncell) return;
     const int s = (int)(idx / ncell);
     const size_t c = idx % ncell;
     const int kind = wall_kind[idx];
     if (kind < 0) {
-        rho_w[idx] = 0.0;
+        if (lane == 0) rho_w[idx] = 0.0;
         return;
     }
     const double rho = mac[c], T = mac[4 * ncell + c];
@@ -253,7 +329,7 @@ __global__ void wall_flux_init_kernel(const double *mac, const int8_t *wall_kind
     const int d = s / 2;
     const double nrm = (s % 2) ? -1.0 : 1.0;  // normal from the wall into the gas
     double F = 0.0;
-    for (int g = 0; g < Nv; g++) {
+    for (int g = lane; g < Nv; g += 32) {
         const double *v = vel64 + (size_t)g * 4;
         const double xn = v[d] * nrm;
         if (!(xn < 0.0)) continue;
@@ -263,7 +339,8 @@ __global__ void wall_flux_init_kernel(const double *mac, const int8_t *wall_kind
         const double fS = A * exp(-c2 / (2.0 * RT)) * (1.0 + (1.0 - Pr) * cq / (5.0 * p * RT) * (c2 / RT - 5.0));
         F += v[3] * (-xn) * fS;
     }
-    rho_w[idx] = F * wall_norm[kind * 6 + s];
+    for (int off = 16; off > 0; off >>= 1) F += __shfl_down_sync(0xffffffffu, F, off);
+    if (lane == 0) rho_w[idx] = F * wall_norm[kind * 6 + s];
 }
 
 __global__ void fill_kernel(double *p, size_t n, double v)
@@ -290,19 +367,20 @@ cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_close(const CloseArgs &a, int n_blocks, cudaStream_t s)
+cudaError_t launch_close(const CloseArgs &a, cudaStream_t s)
 {
+    const unsigned nb = (unsigned)close_blocks(a.ncell);
     if (a.precision == 0)
-        close_kernel<double><<<n_blocks, RED_THREADS, 0, s>>>(a);
+        close_kernel<double><<<nb, CLOSE_CELLS * NPART, 0, s>>>(a);
     else
-        close_kernel<float><<<n_blocks, RED_THREADS, 0, s>>>(a);
+        close_kernel<float><<<nb, CLOSE_CELLS * NPART, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize_mass(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale,
                                  cudaStream_t s)
 {
-    finalize_mass_kernel<<<1, 32, 0, s>>>(blk_mass, n_blocks, M0, rescale, scale);
+    finalize_mass_kernel<<<1, RED_THREADS, 0, s>>>(blk_mass, n_blocks, M0, rescale, scale);
     return cudaGetLastError();
 }
 
@@ -318,7 +396,7 @@ cudaError_t launch_scale_residual(double *mac_new, double *rho_w_new, const doub
 cudaError_t launch_finalize_residual(const double *blk_res, const int *blk_bad, int n_blocks, double *out2,
                                      cudaStream_t s)
 {
-    finalize_residual_kernel<<<1, 32, 0, s>>>(blk_res, blk_bad, n_blocks, out2);
+    finalize_residual_kernel<<<1, RED_THREADS, 0, s>>>(blk_res, blk_bad, n_blocks, out2);
     return cudaGetLastError();
 }
 
@@ -326,8 +404,8 @@ cudaError_t launch_wall_flux_init(const double *mac, const int8_t *wall_kind, co
                                   const double *vel64, int Nv, unsigned long long ncell, double R, double Pr,
                                   double *rho_w, cudaStream_t s)
 {
-    wall_flux_init_kernel<<<nblk(6 * ncell, 128), 128, 0, s>>>(mac, wall_kind, wall_norm, vel64, Nv, ncell, R, Pr,
-                                                                rho_w);
+    wall_flux_init_kernel<<<nblk(6 * ncell, 4), 128, 0, s>>>(mac, wall_kind, wall_norm, vel64, Nv, ncell, R, Pr,
+                                                              rho_w);
     return cudaGetLastError();
 }
 

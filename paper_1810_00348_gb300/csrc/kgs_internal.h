@@ -116,13 +116,17 @@ struct CloseArgs {
     const double *wall_norm;      // [7][6] rho_w = F * wall_norm[kind][side]
     const double *dx, *dy, *dz;
     const uint8_t *solid;         // [ncell] or NULL
-    double *blk_mass;             // [n_blocks]
+    double *blk_mass;             // [close_blocks(ncell)]
 };
 
 cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, const uint8_t *cell_flags_side,
                         const double *rdx, const double *rdy, const double *rdz, int nx, int ny, int nz,
                         double mu_ref, double omega, double Pr, void *coef, cudaStream_t s);
-cudaError_t launch_close(const CloseArgs &a, int n_blocks, cudaStream_t s);
+// Cells per block of the closure kernel; blk_mass holds close_blocks(ncell)
+// values.
+constexpr int CLOSE_CELLS = 16;
+inline size_t close_blocks(size_t ncell) { return (ncell + CLOSE_CELLS - 1) / CLOSE_CELLS; }
+cudaError_t launch_close(const CloseArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_mass(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale,
                                  cudaStream_t s);
 cudaError_t launch_scale_residual(double *mac_new, double *rho_w_new, const double *mac, const uint8_t *solid,

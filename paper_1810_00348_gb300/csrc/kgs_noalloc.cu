@@ -98,7 +98,7 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
     const size_t o_oct = cv.take(3 * 8 * sizeof(int));
     const size_t o_vgoct = cv.take(t.vg_oct.size() * sizeof(int));
     const size_t o_solid = cv.take(t.any_solid ? n : 0);
-    const size_t o_bmass = cv.take(n_red * sizeof(double)), o_bres = cv.take((size_t)n_red * 10 * sizeof(double)),
+    const size_t o_bmass = cv.take(close_blocks(n) * sizeof(double)), o_bres = cv.take((size_t)n_red * 10 * sizeof(double)),
                  o_bbad = cv.take(n_red * sizeof(int)), o_scale = cv.take(2 * sizeof(double)),
                  o_resid = cv.take(2 * sizeof(double));
     if (cv.used > (size_t)KGS_NOALLOC_SCRATCH_BYTES) return KGS_EINVAL;  // too large for the fixed array
@@ -211,8 +211,8 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
     ca.blk_mass = reinterpret_cast<double *>(b + o_bmass);
     double *d_scale = reinterpret_cast<double *>(b + o_scale);
     double *d_resid = reinterpret_cast<double *>(b + o_resid);
-    if (launch_close(ca, n_red, st) != cudaSuccess ||
-        launch_finalize_mass(ca.blk_mass, n_red, M0, M0 > 0.0 ? 1 : 0, d_scale, st) != cudaSuccess ||
+    if (launch_close(ca, st) != cudaSuccess ||
+        launch_finalize_mass(ca.blk_mass, (int)close_blocks(n), M0, M0 > 0.0 ? 1 : 0, d_scale, st) != cudaSuccess ||
         launch_scale_residual(macros_out, rho_w_out, macros_in, d_solid, n, d_scale,
                               reinterpret_cast<double *>(b + o_bres), reinterpret_cast<int *>(b + o_bbad), n_red,
                               st) != cudaSuccess ||

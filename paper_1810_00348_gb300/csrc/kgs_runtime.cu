@@ -220,8 +220,8 @@ int kgs::ctx_launch_closure(kgs_ctx *c, double *resid_dev)
     ca.dz = c->ddz;
     ca.solid = c->solid;
     ca.blk_mass = c->blk_mass;
-    KGS_CHECK(launch_close(ca, c->n_red_blocks, st));
-    KGS_CHECK(launch_finalize_mass(c->blk_mass, c->n_red_blocks, c->M0, c->mass_rescale, c->scale, st));
+    KGS_CHECK(launch_close(ca, st));
+    KGS_CHECK(launch_finalize_mass(c->blk_mass, (int)close_blocks(t.ncell), c->M0, c->mass_rescale, c->scale, st));
     KGS_CHECK(launch_scale_residual(c->mac_new, c->rho_w_new, c->mac, c->solid, t.ncell, c->scale, c->blk_res,
                                     c->blk_bad, c->n_red_blocks, st));
     KGS_CHECK(launch_finalize_residual(c->blk_res, c->blk_bad, c->n_red_blocks, resid_dev, st));
@@ -330,7 +330,7 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
         (rc = upload(c, &c->d_vstart, std::vector<int>(t.oct_vstart, t.oct_vstart + 8))) ||
         (rc = upload(c, &c->d_vcount, std::vector<int>(t.oct_vcount, t.oct_vcount + 8))) ||
         (rc = upload(c, &c->d_vgbase, std::vector<int>(t.oct_vgbase, t.oct_vgbase + 8))) ||
-        (rc = upload(c, &c->d_vg_oct, t.vg_oct)) || (rc = dalloc_t(c, &c->blk_mass, c->n_red_blocks)) ||
+        (rc = upload(c, &c->d_vg_oct, t.vg_oct)) || (rc = dalloc_t(c, &c->blk_mass, close_blocks(n))) ||
         (rc = dalloc_t(c, &c->blk_res, (size_t)c->n_red_blocks * 10)) ||
         (rc = dalloc_t(c, &c->blk_bad, c->n_red_blocks)) || (rc = dalloc_t(c, &c->scale, 2)) ||
         (rc = dalloc_t(c, &c->resid, 2)))
