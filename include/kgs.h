@@ -266,6 +266,66 @@ int kgs_batch_profile(kgs_batch *b, double *sweep_ms, long long *sweeps, long lo
 int kgs_batch_fault(kgs_batch *b, long long spin_limit, int unpublished_item);
 void kgs_batch_destroy(kgs_batch *b);
 
+/* ---- learned initial guess ----
+ * The paper starts every solve from a uniform state and notes that the
+ * iteration converges slowly at small Knudsen number (Section 4.1); this
+ * library adds a learned starting field.  A stack of 3x3x3 convolutions
+ * (zero padding, bias, ReLU between layers) maps 11 channels per cell --
+ * log Kn, 10 U_lid, the solid flag and the normalised trilinear upsampling of
+ * a coarse-grid solution -- to a normalised correction of the 8 macroscopic
+ * fields over that upsampling.  Normalisation of field c (order rho, Ux, Uy,
+ * Uz, T, qx, qy, qz): n_c = s_c (m_c - r_c) with r = (1,0,0,0,1,0,0,0) and
+ * s = (10,10,10,10,50,100,100,100); corrections are scaled by s_c alone.
+ *
+ * Tensors are device arrays, channels last: x[B][D][H][W][C] with D = nz,
+ * H = ny, W = nx.  Weights and stored activations are bfloat16, products
+ * accumulate in FP32 on the tensor cores; the master parameters and Adam
+ * moments are FP32.  Channel counts are at most 112.  A network is bound to
+ * the device current at creation and works on `stream` (NULL = legacy
+ * default stream); calls are ordered on that stream and the functions that
+ * return host values synchronise it.  Parameter layout on the host (get/set):
+ * per layer W[27][Cout][Cin] (tap t = (kz*3 + ky)*3 + kx reads the input at
+ * offset (kz-1, ky-1, kx-1)) followed by b[Cout], FP32. */
+typedef struct kgs_net kgs_net;
+
+/* channels[n_layers + 1]: input, hidden..., output.  Weights He-normal from
+ * a splitmix64 stream seeded by `seed` (the last layer scaled by 0.1), biases
+ * zero.  KGS_EINVAL for a channel count outside [1, 112]. */
+int kgs_net_create(kgs_net **out, int n_layers, const int *channels, unsigned long long seed, void *stream);
+/* Parameter counts without and with the padding of channels to 16. */
+int kgs_net_num_params(kgs_net *net, long long *real, long long *padded);
+/* what = 0: parameters, 1: gradients of the last kgs_net_train_step; host. */
+int kgs_net_get(kgs_net *net, int what, float *host);
+/* Replace the parameters (host) and reset the optimiser state. */
+int kgs_net_set_params(kgs_net *net, const float *host);
+/* y[B][D][H][W][Cout] (FP32, device) for x[B][D][H][W][Cin] (FP32, device). */
+int kgs_net_forward(kgs_net *net, const float *x, int B, int D, int H, int W, float *y);
+/* One training step on the mean squared error over the voxels with
+ * mask != 0 (mask: device bytes [B][D][H][W], NULL = all) and the output
+ * channels, target[B][D][H][W][Cout] (FP32, device): forward, backward,
+ * then Adam (beta 0.9 / 0.999, eps 1e-8) with step lr; lr <= 0 computes the
+ * gradients only.  *loss (host, may be NULL) receives the loss of the
+ * parameters before the update. */
+int kgs_net_train_step(kgs_net *net, const float *x, const float *target, const uint8_t *mask, int B, int D, int H,
+                       int W, float lr, float *loss);
+void kgs_net_destroy(kgs_net *net);
+
+/* Features of one instance: coarse[8][nzc][nyc][nxc] (device FP64, a
+ * solution on a grid of equal-width cells covering the same box) is
+ * upsampled trilinearly between cell centres (clamped at the outer centres)
+ * to up[8][nz][ny][nx] (device FP64); x[nz][ny][nx][11] (device FP32)
+ * receives (log kn, 10 u_lid, solid flag, normalised up).  solid: device
+ * bytes [nz][ny][nx] or NULL. */
+int kgs_surrogate_features(int nx, int ny, int nz, int nxc, int nyc, int nzc, const double *coarse,
+                           const uint8_t *solid, double kn, double u_lid, float *x, double *up, void *stream);
+/* Training target[ncell][8] = s_c (fine - up) (device; fine, up [8][ncell]). */
+int kgs_surrogate_target(long long ncell, const double *fine, const double *up, float *target, void *stream);
+/* Initial guess macros[8][ncell] = up + y / s_c (device), y[ncell][8] the
+ * network output; *n_bad (host) receives the number of cells whose guess is
+ * not a physical state (non-finite, rho <= 0 or T <= 0): a caller rejects
+ * such a guess and starts from the uniform state.  Synchronises `stream`. */
+int kgs_surrogate_apply(long long ncell, const double *up, const float *y, double *macros, int *n_bad, void *stream);
+
 /* ---- iteration without device allocation ----
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory themselves or through this library:

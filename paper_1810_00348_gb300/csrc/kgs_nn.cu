@@ -1,0 +1,889 @@
+// kgs_nn.cu -- the 3D convolutional surrogate that supplies the initial
+// macroscopic fields of a solve: inference and training kernels.
+//
+// Volumes are channels-last, act[b][z][y][x][Cp] with Cp the channel count
+// padded to a multiple of 16; stored activations and weights are bfloat16,
+// every product is accumulated in FP32.  A layer is a 3x3x3 convolution with
+// zero padding, bias, and ReLU except on the last layer.  As a GEMM it is
+// out[v][co] = sum_{t, ci} in[v + off(t)][ci] W[t][co][ci] (M = voxels,
+// N = output channels, K = 27 * input channels); the kernels run it on the
+// tensor cores with mma.sync m16n8k16 (BF16 in, FP32 accumulate), operands
+// staged in shared memory and fed with ldmatrix:
+//   conv_fwd    forward, and the data gradient of the backward pass (the same
+//               GEMM with the taps mirrored and the channel roles swapped),
+//               with bias + ReLU, or the ReLU-derivative mask, in the epilogue;
+//   conv_wgrad  weight gradient, per tap a GEMM over voxels (M = Cout,
+//               N = Cin, K = voxels), split over voxel chunks whose partial
+//               sums are added in a fixed order;
+// plus bias gradients, the masked mean-squared-error loss, Adam, and the
+// feature / target / prediction maps between the solver's FP64 fields and the
+// network's normalised channels.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/kgs.h"
+
+namespace {
+
+constexpr int TILE = 4;                 // spatial tile edge: 4^3 = 64 voxels per CTA
+constexpr int TV_ = TILE * TILE * TILE; // voxels per tile
+constexpr int HALO = TILE + 2;          // tile with the 1-voxel halo
+constexpr int HV = HALO * HALO * HALO;  // 216 halo voxels
+constexpr int CONV_THREADS = 128;       // 4 warps x 16 voxels
+constexpr int WG_CHUNK_TILES = 32;      // voxel tiles per weight-gradient CTA
+constexpr int WG_TILES_PER_WARP = 25;   // ceil((112/16) * (112/8) / 4) output tiles
+
+__host__ __device__ inline int pad16(int c) { return (c + 15) / 16 * 16; }
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                         unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+struct ConvDims {
+    int B, D, H, W;  // batch and volume
+    int cin_p, cout_p;
+};
+
+// ---------------------------------------------------------------------------
+// Forward (and data-gradient) convolution.
+//   in   [B][D][H][W][cin_p]   bf16
+//   w    [27][cout_p][cin_p]   bf16 (per tap: output-channel rows, input channels contiguous)
+//   bias [cout_p] FP32 or NULL
+//   MODE 0: out = relu(acc + bias) -> bf16
+//   MODE 1: out = acc + bias -> FP32 (last layer)
+//   MODE 2: out = acc * (gate > 0) -> bf16 (ReLU derivative of the layer below,
+//           gate = that layer's stored activation, same layout as out)
+// CTA: one 4x4x4 voxel tile of one sample, all output channels.  Warp w owns
+// voxels 16w..16w+15 of the tile; per k-step of 16 input channels it issues
+// cout_p/8 mma over the tap's shifted voxels.
+template <int MODE>
+__global__ void __launch_bounds__(CONV_THREADS) conv_fwd_kernel(const __nv_bfloat16 *__restrict__ in,
+                                                                const __nv_bfloat16 *__restrict__ w,
+                                                                const float *__restrict__ bias, void *out,
+                                                                const __nv_bfloat16 *__restrict__ gate, ConvDims dm)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int cin_p = dm.cin_p, cout_p = dm.cout_p;
+    const int hs = cin_p + 8;   // halo row stride (bf16): +16 bytes against bank conflicts
+    const int ws = cin_p + 8;   // weight row stride
+    __nv_bfloat16 *halo = reinterpret_cast<__nv_bfloat16 *>(sm);             // [HV][hs]
+    __nv_bfloat16 *wt = halo + HV * hs;                                      // [2][cout_p][ws]
+    const int tiles_x = (dm.W + TILE - 1) / TILE, tiles_y = (dm.H + TILE - 1) / TILE;
+    const int tx = blockIdx.x % tiles_x, ty = (blockIdx.x / tiles_x) % tiles_y, tz = blockIdx.x / (tiles_x * tiles_y);
+    const int b = blockIdx.y;
+    const int x0 = tx * TILE - 1, y0 = ty * TILE - 1, z0 = tz * TILE - 1;
+    const size_t vol = (size_t)dm.D * dm.H * dm.W;
+    const __nv_bfloat16 *inb = in + (size_t)b * vol * cin_p;
+
+    // halo tile (zero outside the volume), 16-byte chunks
+    const int cch = cin_p / 8;
+    for (int i = threadIdx.x; i < HV * cch; i += CONV_THREADS) {
+        const int hv = i / cch, ch = i % cch;
+        const int hx = hv % HALO, hy = (hv / HALO) % HALO, hz = hv / (HALO * HALO);
+        const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (gx >= 0 && gy >= 0 && gz >= 0 && gx < dm.W && gy < dm.H && gz < dm.D)
+            val = *reinterpret_cast<const uint4 *>(inb + (((size_t)gz * dm.H + gy) * dm.W + gx) * cin_p + ch * 8);
+        *reinterpret_cast<uint4 *>(halo + hv * hs + ch * 8) = val;
+    }
+    auto load_w = [&](int t, int buf) {
+        const __nv_bfloat16 *src = w + (size_t)t * cout_p * cin_p;
+        __nv_bfloat16 *dst = wt + (size_t)buf * cout_p * ws;
+        for (int i = threadIdx.x; i < cout_p * cch; i += CONV_THREADS) {
+            const int r = i / cch, ch = i % cch;
+            *reinterpret_cast<uint4 *>(dst + r * ws + ch * 8) =
+                *reinterpret_cast<const uint4 *>(src + (size_t)r * cin_p + ch * 8);
+        }
+    };
+    load_w(0, 0);
+    __syncthreads();
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int ntile = cout_p / 8;  // n8 tiles
+    float acc[14][4];              // cout_p <= 112
+#pragma unroll
+    for (int j = 0; j < 14; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    // this lane's A row (ldmatrix x4: rows 0-15 of the warp's block, k halves)
+    const int arow = (lane & 7) + ((lane >> 3) & 1) * 8;
+    const int akof = (lane >> 4) * 8;
+    const int m = warp * 16 + arow;  // voxel of the tile
+    const int lx = m % TILE, ly = (m / TILE) % TILE, lz = m / (TILE * TILE);
+    // B rows (ldmatrix x4 over two n8 tiles): n = (lane & 7) + (lane >> 4) * 8, k half by bit 3
+    const int brow = (lane & 7) + (lane >> 4) * 8;
+    const int bkof = ((lane >> 3) & 1) * 8;
+
+    for (int t = 0; t < 27; t++) {
+        const int buf = t & 1;
+        if (t + 1 < 27) load_w(t + 1, buf ^ 1);
+        const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
+        const int hv = ((lz + kz) * HALO + (ly + ky)) * HALO + (lx + kx);
+        const __nv_bfloat16 *arowp = halo + hv * hs + akof;
+        const __nv_bfloat16 *wb = wt + (size_t)buf * cout_p * ws;
+        for (int kc = 0; kc < cin_p; kc += 16) {
+            unsigned a0, a1, a2, a3;
+            ldsm_x4(smem_addr(arowp + kc), a0, a1, a2, a3);
+#pragma unroll
+            for (int j2 = 0; j2 < 7; j2++) {
+                if (2 * j2 >= ntile) break;
+                unsigned b0, b1, b2, b3;
+                ldsm_x4(smem_addr(wb + (j2 * 16 + brow) * ws + kc + bkof), b0, b1, b2, b3);
+                mma_bf16(acc[2 * j2], a0, a1, a2, a3, b0, b1);
+                if (2 * j2 + 1 < ntile) mma_bf16(acc[2 * j2 + 1], a0, a1, a2, a3, b2, b3);
+            }
+        }
+        __syncthreads();  // next tap's weights loaded, this tap's done
+    }
+
+    // epilogue: rows g and g+8 of the warp's 16 voxels, columns 2*(lane%4)+{0,1}
+    const int g = lane >> 2, cpair = (lane & 3) * 2;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        const int mm = warp * 16 + g + half * 8;
+        const int vx = tx * TILE + mm % TILE, vy = ty * TILE + (mm / TILE) % TILE, vz = tz * TILE + mm / (TILE * TILE);
+        if (vx >= dm.W || vy >= dm.H || vz >= dm.D) continue;
+        const size_t vo = (size_t)b * vol + ((size_t)vz * dm.H + vy) * dm.W + vx;
+#pragma unroll
+        for (int j = 0; j < 14; j++) {
+            if (j >= ntile) break;
+            const int co = j * 8 + cpair;
+            float v0 = acc[j][half * 2], v1 = acc[j][half * 2 + 1];
+            if (MODE != 2 && bias) {
+                v0 += bias[co];
+                v1 += bias[co + 1];
+            }
+            if (MODE == 0) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+                reinterpret_cast<__nv_bfloat162 *>(out)[(vo * cout_p + co) / 2] = __floats2bfloat162_rn(v0, v1);
+            } else if (MODE == 1) {
+                reinterpret_cast<float2 *>(out)[(vo * cout_p + co) / 2] = make_float2(v0, v1);
+            } else {
+                const __nv_bfloat162 gt = reinterpret_cast<const __nv_bfloat162 *>(gate)[(vo * cout_p + co) / 2];
+                v0 = __bfloat162float(gt.x) > 0.f ? v0 : 0.f;
+                v1 = __bfloat162float(gt.y) > 0.f ? v1 : 0.f;
+                reinterpret_cast<__nv_bfloat162 *>(out)[(vo * cout_p + co) / 2] = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient: part[chunk][t][co][ci] = sum over the chunk's voxels v of
+// dy[v][co] * in[v + off(t)][ci].  CTA = (tap, chunk of WG_CHUNK_TILES tiles,
+// sample).  Per tile: dy tile [64 voxels][cout_p] and the input halo in shared
+// memory; A = dy^T (co x v) and B = in (v x ci) through transposing ldmatrix.
+__global__ void __launch_bounds__(CONV_THREADS) conv_wgrad_kernel(const __nv_bfloat16 *__restrict__ in,
+                                                                  const __nv_bfloat16 *__restrict__ dy,
+                                                                  float *__restrict__ part, ConvDims dm,
+                                                                  int n_chunks)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int cin_p = dm.cin_p, cout_p = dm.cout_p;
+    const int hs = cin_p + 8, ds = cout_p + 8;
+    __nv_bfloat16 *halo = reinterpret_cast<__nv_bfloat16 *>(sm);  // [HV][hs]
+    __nv_bfloat16 *dys = halo + HV * hs;                           // [64][ds]
+    const int t = blockIdx.x;
+    const int chunk = blockIdx.y, b = blockIdx.z;
+    const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
+    const int tiles_x = (dm.W + TILE - 1) / TILE, tiles_y = (dm.H + TILE - 1) / TILE,
+              tiles_z = (dm.D + TILE - 1) / TILE;
+    const int n_tiles = tiles_x * tiles_y * tiles_z;
+    const size_t vol = (size_t)dm.D * dm.H * dm.W;
+    const int cch = cin_p / 8, dch = cout_p / 8;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    // output tiles (m16 x n8) of the Cout x Cin block, spread over the warps
+    const int mt = cout_p / 16, nt = cin_p / 8;
+    const int n_out = mt * nt;
+    float acc[WG_TILES_PER_WARP][4];
+#pragma unroll
+    for (int j = 0; j < WG_TILES_PER_WARP; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+
+    for (int it = 0; it < WG_CHUNK_TILES; it++) {
+        const int tile = chunk * WG_CHUNK_TILES + it;
+        if (tile >= n_tiles) break;
+        const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, tz = tile / (tiles_x * tiles_y);
+        __syncthreads();  // previous tile's operands are consumed
+        // input halo
+        for (int i = threadIdx.x; i < HV * cch; i += CONV_THREADS) {
+            const int hv = i / cch, ch = i % cch;
+            const int gx = tx * TILE - 1 + hv % HALO, gy = ty * TILE - 1 + (hv / HALO) % HALO,
+                      gz = tz * TILE - 1 + hv / (HALO * HALO);
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (gx >= 0 && gy >= 0 && gz >= 0 && gx < dm.W && gy < dm.H && gz < dm.D)
+                val = *reinterpret_cast<const uint4 *>(in + ((size_t)b * vol + ((size_t)gz * dm.H + gy) * dm.W + gx) *
+                                                                 cin_p + ch * 8);
+            *reinterpret_cast<uint4 *>(halo + hv * hs + ch * 8) = val;
+        }
+        // dy tile (zero outside the volume)
+        for (int i = threadIdx.x; i < TV_ * dch; i += CONV_THREADS) {
+            const int mm = i / dch, ch = i % dch;
+            const int gx = tx * TILE + mm % TILE, gy = ty * TILE + (mm / TILE) % TILE, gz = tz * TILE + mm / (TILE * TILE);
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (gx < dm.W && gy < dm.H && gz < dm.D)
+                val = *reinterpret_cast<const uint4 *>(dy + ((size_t)b * vol + ((size_t)gz * dm.H + gy) * dm.W + gx) *
+                                                                cout_p + ch * 8);
+            *reinterpret_cast<uint4 *>(dys + mm * ds + ch * 8) = val;
+        }
+        __syncthreads();
+        // K = 64 voxels of the tile, 16 at a time
+        for (int k0 = 0; k0 < TV_; k0 += 16) {
+            // A (co x v) row-major from dys[v][co], transposed by ldmatrix:
+            // matrices (co 0-7 | 8-15) x (v 0-7 | 8-15)
+            const int av = k0 + (lane & 7) + (lane >> 4) * 8;
+            const int aco = ((lane >> 3) & 1) * 8;
+            // B (v x ci) from halo[v + off(t)][ci], transposed: v 0-7 | 8-15
+            const int bv = k0 + (lane & 7) + ((lane >> 3) & 1) * 8;
+            const int blx = bv % TILE, bly = (bv / TILE) % TILE, blz = bv / (TILE * TILE);
+            const int bhv = ((blz + kz) * HALO + (bly + ky)) * HALO + (blx + kx);
+#pragma unroll
+            for (int j = 0; j < WG_TILES_PER_WARP; j++) {
+                const int o = warp + 4 * j;
+                if (o < n_out) {
+                    const int mi = o / nt, ni = o % nt;
+                    unsigned a0, a1, a2, a3, b0, b1, b2, b3;
+                    ldsm_x4_t(smem_addr(dys + av * ds + mi * 16 + aco), a0, a1, a2, a3);
+                    ldsm_x4_t(smem_addr(halo + bhv * hs + ni * 8), b0, b1, b2, b3);
+                    (void)b2;
+                    (void)b3;
+                    mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+                }
+            }
+        }
+    }
+    // write the chunk's partial: part[((b*n_chunks + chunk) * 27 + t)][co][ci]
+    float *dst = part + (((size_t)b * n_chunks + chunk) * 27 + t) * cout_p * cin_p;
+    const int g = lane >> 2, cpair = (lane & 3) * 2;
+#pragma unroll
+    for (int j = 0; j < WG_TILES_PER_WARP; j++) {
+        const int o = warp + 4 * j;
+        if (o < n_out) {
+            const int mi = o / nt, ni = o % nt;
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                const int co = mi * 16 + g + half * 8, ci = ni * 8 + cpair;
+                *reinterpret_cast<float2 *>(dst + co * cin_p + ci) = make_float2(acc[j][half * 2], acc[j][half * 2 + 1]);
+            }
+        }
+    }
+}
+
+// gW[t][co][ci] = sum over (sample, chunk) in order of the partials.
+__global__ void wgrad_reduce_kernel(const float *__restrict__ part, int n_parts, size_t per, float *__restrict__ gw)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= per) return;
+    float s = 0.f;
+    for (int p = 0; p < n_parts; p++) s += part[(size_t)p * per + i];
+    gw[i] = s;
+}
+
+// Bias gradient gb[co] = sum over voxels of dy[v][co]: one block per channel,
+// strided per-thread sums then a tree (fixed order).
+template <typename T>
+__global__ void bias_grad_kernel(const T *__restrict__ dy, size_t nvox, int cp, float *__restrict__ gb)
+{
+    __shared__ float sh[256];
+    const int co = blockIdx.x;
+    float s = 0.f;
+    for (size_t v = threadIdx.x; v < nvox; v += 256) s += (float)dy[v * cp + co];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gb[co] = sh[0];
+}
+
+// Wt[26-t][ci][co] = W[t][co][ci]: weights of the data-gradient convolution.
+__global__ void transpose_w_kernel(const __nv_bfloat16 *__restrict__ w, int cout_p, int cin_p,
+                                   __nv_bfloat16 *__restrict__ wt)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t per = (size_t)cout_p * cin_p;
+    if (i >= 27 * per) return;
+    const int t = (int)(i / per), r = (int)(i % per), co = r / cin_p, ci = r % cin_p;
+    wt[(size_t)(26 - t) * per + (size_t)ci * cout_p + co] = w[i];
+}
+
+// Masked mean squared error over the real output channels: per-block partial
+// sums (fixed order) and the gradient dy = 2 (y - t) m / count as bf16.
+__global__ void mse_kernel(const float *__restrict__ y, const float *__restrict__ tgt, const uint8_t *__restrict__ mask,
+                           size_t nvox, int cp, int cout, float inv_count, __nv_bfloat16 *__restrict__ dy,
+                           float *__restrict__ part)
+{
+    __shared__ float sh[256];
+    float s = 0.f;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nvox) {
+        const float mk = (mask == nullptr || mask[i]) ? 1.f : 0.f;
+        for (int c = 0; c < cp; c++) {
+            float g = 0.f;
+            if (c < cout) {
+                const float d = (y[i * cp + c] - tgt[i * cout + c]) * mk;
+                s += d * d;
+                g = 2.f * d * inv_count;
+            }
+            dy[i * cp + c] = __float2bfloat16_rn(g);
+        }
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// Adam on the FP32 master parameters (padding entries stay zero: their
+// gradients are zero), and the bf16 copy used by the convolutions.
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m1,
+                            float *__restrict__ m2, __nv_bfloat16 *__restrict__ pb, size_t n, float lr, float b1,
+                            float b2, float eps, float c1, float c2)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float pi = p[i] - lr * (a / c1) / (sqrtf(v / c2) + eps);
+    p[i] = pi;
+    if (pb) pb[i] = __float2bfloat16_rn(pi);
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ x, size_t n, __nv_bfloat16 *__restrict__ y)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// Input channels-last FP32 [vox][c0] -> bf16 [vox][cp] (padding zero).
+__global__ void pack_input_kernel(const float *__restrict__ x, size_t nvox, int c0, int cp,
+                                  __nv_bfloat16 *__restrict__ y)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvox * cp) return;
+    const size_t v = i / cp;
+    const int c = (int)(i % cp);
+    y[i] = __float2bfloat16_rn(c < c0 ? x[v * c0 + c] : 0.f);
+}
+
+// Output FP32 [vox][cp] -> [vox][cout].
+__global__ void unpack_output_kernel(const float *__restrict__ y, size_t nvox, int cp, int cout, float *__restrict__ out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvox * cout) return;
+    out[i] = y[(i / cout) * cp + i % cout];
+}
+
+// ---------------------------------------------------------------------------
+// Maps between the solver's macroscopic fields ([8][nz][ny][nx] FP64: rho,
+// Ux, Uy, Uz, T, qx, qy, qz) and the network's normalised channels.  Each
+// field c is scaled about its rest value: n_c = s_c (m_c - r_c) with
+// r = (1, 0, 0, 0, 1, 0, 0, 0) and s = (10, 10, 10, 10, 50, 100, 100, 100),
+// so that fields of a low-speed flow are O(1) in the network.
+__constant__ float c_scale[8] = {10.f, 10.f, 10.f, 10.f, 50.f, 100.f, 100.f, 100.f};
+__constant__ double c_rest[8] = {1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 0.0};
+
+__device__ inline void up_axis(int i, int n, int nc, int &i0, int &i1, double &t)
+{
+    // cell centres of equal-width cells: fine centre (i + 1/2)/n lies at
+    // coarse index (i + 1/2) nc / n - 1/2, clamped to the outermost centres
+    double u = ((double)i + 0.5) * nc / n - 0.5;
+    u = fmin(fmax(u, 0.0), (double)(nc - 1));
+    i0 = (int)floor(u);
+    i1 = min(i0 + 1, nc - 1);
+    t = u - i0;
+}
+
+// Features of one instance: x[z][y][x][11] = (log Kn, 10 U_lid, solid,
+// normalised upsampled coarse fields) and the upsampled fields themselves.
+__global__ void features_kernel(int nx, int ny, int nz, int nxc, int nyc, int nzc, const double *__restrict__ coarse,
+                                const uint8_t *__restrict__ solid, float log_kn, float u_lid, float *__restrict__ x,
+                                double *__restrict__ up)
+{
+    const size_t cell = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t ncell = (size_t)nx * ny * nz;
+    if (cell >= ncell) return;
+    const int i = (int)(cell % nx), j = (int)((cell / nx) % ny), k = (int)(cell / ((size_t)nx * ny));
+    int i0, i1, j0, j1, k0, k1;
+    double tx, ty, tz;
+    up_axis(i, nx, nxc, i0, i1, tx);
+    up_axis(j, ny, nyc, j0, j1, ty);
+    up_axis(k, nz, nzc, k0, k1, tz);
+    const size_t ncc = (size_t)nxc * nyc * nzc;
+    float *xo = x + cell * 11;
+    xo[0] = log_kn;
+    xo[1] = 10.f * u_lid;
+    xo[2] = solid ? (float)(solid[cell] != 0) : 0.f;
+    for (int c = 0; c < 8; c++) {
+        const double *f = coarse + c * ncc;
+        auto at = [&](int kk, int jj, int ii) { return f[((size_t)kk * nyc + jj) * nxc + ii]; };
+        const double v0 = (1 - tx) * at(k0, j0, i0) + tx * at(k0, j0, i1);
+        const double v1 = (1 - tx) * at(k0, j1, i0) + tx * at(k0, j1, i1);
+        const double v2 = (1 - tx) * at(k1, j0, i0) + tx * at(k1, j0, i1);
+        const double v3 = (1 - tx) * at(k1, j1, i0) + tx * at(k1, j1, i1);
+        const double v = (1 - tz) * ((1 - ty) * v0 + ty * v1) + tz * ((1 - ty) * v2 + ty * v3);
+        up[c * ncell + cell] = v;
+        xo[3 + c] = (float)(c_scale[c] * (v - c_rest[c]));
+    }
+}
+
+// Training target: the normalised correction t[cell][c] = s_c (fine - up).
+__global__ void target_kernel(size_t ncell, const double *__restrict__ fine, const double *__restrict__ up,
+                              float *__restrict__ t)
+{
+    const size_t cell = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= ncell) return;
+    for (int c = 0; c < 8; c++) t[cell * 8 + c] = (float)(c_scale[c] * (fine[c * ncell + cell] - up[c * ncell + cell]));
+}
+
+// Initial guess m = up + y / s, and the count of cells where it is not a
+// physical state (non-finite, rho <= 0 or T <= 0).
+__global__ void apply_kernel(size_t ncell, const double *__restrict__ up, const float *__restrict__ y,
+                             double *__restrict__ m, int *__restrict__ n_bad)
+{
+    const size_t cell = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= ncell) return;
+    bool bad = false;
+    for (int c = 0; c < 8; c++) {
+        const double v = up[c * ncell + cell] + (double)y[cell * 8 + c] / c_scale[c];
+        m[c * ncell + cell] = v;
+        bad |= !isfinite(v);
+        if (c == 0 || c == 4) bad |= !(v > 0.0);
+    }
+    if (bad) atomicAdd(n_bad, 1);
+}
+
+inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+size_t conv_fwd_smem(int cin_p, int cout_p)
+{
+    return (size_t)HV * (cin_p + 8) * 2 + 2 * (size_t)cout_p * (cin_p + 8) * 2;
+}
+
+size_t wgrad_smem(int cin_p, int cout_p) { return (size_t)HV * (cin_p + 8) * 2 + (size_t)TV_ * (cout_p + 8) * 2; }
+
+template <int MODE>
+cudaError_t run_conv(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
+                     const __nv_bfloat16 *gate, ConvDims dm, cudaStream_t s)
+{
+    const size_t smem = conv_fwd_smem(dm.cin_p, dm.cout_p);
+    cudaError_t e = cudaFuncSetAttribute(conv_fwd_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((dm.W + TILE - 1) / TILE) * ((dm.H + TILE - 1) / TILE) * ((dm.D + TILE - 1) / TILE);
+    conv_fwd_kernel<MODE><<<dim3(tiles, dm.B), CONV_THREADS, smem, s>>>(in, w, bias, out, gate, dm);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// network object
+
+struct kgs_net {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int L = 0;
+    std::vector<int> c, cp;             // real and padded channels per level (L + 1)
+    std::vector<size_t> w_off, b_off;   // offsets into the flat parameter arrays
+    size_t n_params = 0;                // padded parameter count
+    float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;  // FP32 master, grad, Adam moments
+    __nv_bfloat16 *pb = nullptr;        // bf16 copy of the parameters
+    __nv_bfloat16 *wt = nullptr;        // transposed weights of one layer (data gradient)
+    long long step = 0;
+    // activation storage for the current shape
+    int B = 0, D = 0, H = 0, W = 0;
+    std::vector<__nv_bfloat16 *> act;   // L bf16 tensors: input, hidden outputs
+    float *out = nullptr;               // last layer FP32 [vox][cp[L]]
+    __nv_bfloat16 *ga = nullptr, *gb2 = nullptr;  // gradient ping-pong (bf16)
+    float *wpart = nullptr;
+    size_t wpart_cap = 0;
+    float *loss_part = nullptr;
+    size_t loss_part_cap = 0;
+    float *h_loss = nullptr;
+};
+
+namespace {
+
+int err(cudaError_t e)
+{
+    if (e == cudaSuccess) return KGS_OK;
+    if (e == cudaErrorMemoryAllocation) return KGS_ENOMEM;
+    return KGS_ECUDA;
+}
+
+#define NN_CHECK(x)                        \
+    do {                                   \
+        cudaError_t e_ = (x);              \
+        if (e_ != cudaSuccess) return err(e_); \
+    } while (0)
+
+void free_acts(kgs_net *n)
+{
+    for (auto *a : n->act) cudaFree(a);
+    n->act.clear();
+    if (n->out) cudaFree(n->out);
+    if (n->ga) cudaFree(n->ga);
+    if (n->gb2) cudaFree(n->gb2);
+    n->out = nullptr;
+    n->ga = n->gb2 = nullptr;
+    n->B = n->D = n->H = n->W = 0;
+}
+
+int ensure_shape(kgs_net *n, int B, int D, int H, int W)
+{
+    if (n->B == B && n->D == D && n->H == H && n->W == W) return KGS_OK;
+    free_acts(n);
+    const size_t nvox = (size_t)B * D * H * W;
+    int cmax = 0;
+    for (int l = 0; l <= n->L; l++) cmax = std::max(cmax, n->cp[l]);
+    n->act.assign(n->L, nullptr);
+    for (int l = 0; l < n->L; l++) NN_CHECK(cudaMalloc(&n->act[l], nvox * n->cp[l] * sizeof(__nv_bfloat16)));
+    NN_CHECK(cudaMalloc(&n->out, nvox * n->cp[n->L] * sizeof(float)));
+    NN_CHECK(cudaMalloc(&n->ga, nvox * cmax * sizeof(__nv_bfloat16)));
+    NN_CHECK(cudaMalloc(&n->gb2, nvox * cmax * sizeof(__nv_bfloat16)));
+    n->B = B;
+    n->D = D;
+    n->H = H;
+    n->W = W;
+    return KGS_OK;
+}
+
+ConvDims dims(const kgs_net *n, int l) { return ConvDims{n->B, n->D, n->H, n->W, n->cp[l], n->cp[l + 1]}; }
+
+int forward(kgs_net *n, const float *x)
+{
+    cudaStream_t s = n->stream;
+    const size_t nvox = (size_t)n->B * n->D * n->H * n->W;
+    pack_input_kernel<<<nblk(nvox * n->cp[0], 256), 256, 0, s>>>(x, nvox, n->c[0], n->cp[0], n->act[0]);
+    NN_CHECK(cudaGetLastError());
+    for (int l = 0; l < n->L; l++) {
+        const __nv_bfloat16 *w = n->pb + n->w_off[l];
+        const float *bias = n->p + n->b_off[l];
+        if (l < n->L - 1)
+            NN_CHECK(run_conv<0>(n->act[l], w, bias, n->act[l + 1], nullptr, dims(n, l), s));
+        else
+            NN_CHECK(run_conv<1>(n->act[l], w, bias, n->out, nullptr, dims(n, l), s));
+    }
+    return KGS_OK;
+}
+
+// Gradients of all parameters for the upstream gradient held in n->ga
+// (bf16, [vox][cp[L]]), after forward().
+int backward(kgs_net *n)
+{
+    cudaStream_t s = n->stream;
+    const size_t nvox = (size_t)n->B * n->D * n->H * n->W;
+    const int tiles = ((n->W + TILE - 1) / TILE) * ((n->H + TILE - 1) / TILE) * ((n->D + TILE - 1) / TILE);
+    const int n_chunks = (tiles + WG_CHUNK_TILES - 1) / WG_CHUNK_TILES;
+    __nv_bfloat16 *gcur = n->ga, *gnext = n->gb2;
+    for (int l = n->L - 1; l >= 0; l--) {
+        const ConvDims dm = dims(n, l);
+        const size_t per = (size_t)27 * dm.cout_p * dm.cin_p;
+        // weight gradient
+        const size_t need = (size_t)n->B * n_chunks * per;
+        if (need > n->wpart_cap) {
+            if (n->wpart) cudaFree(n->wpart);
+            n->wpart = nullptr;
+            NN_CHECK(cudaMalloc(&n->wpart, need * sizeof(float)));
+            n->wpart_cap = need;
+        }
+        const size_t smem = wgrad_smem(dm.cin_p, dm.cout_p);
+        NN_CHECK(cudaFuncSetAttribute(conv_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        conv_wgrad_kernel<<<dim3(27, n_chunks, n->B), CONV_THREADS, smem, s>>>(n->act[l], gcur, n->wpart, dm, n_chunks);
+        NN_CHECK(cudaGetLastError());
+        wgrad_reduce_kernel<<<nblk(per, 256), 256, 0, s>>>(n->wpart, n->B * n_chunks, per, n->g + n->w_off[l]);
+        NN_CHECK(cudaGetLastError());
+        bias_grad_kernel<__nv_bfloat16><<<dm.cout_p, 256, 0, s>>>(gcur, nvox, dm.cout_p, n->g + n->b_off[l]);
+        NN_CHECK(cudaGetLastError());
+        if (l == 0) break;
+        // data gradient into layer l's input, masked by that layer's ReLU
+        transpose_w_kernel<<<nblk(per, 256), 256, 0, s>>>(n->pb + n->w_off[l], dm.cout_p, dm.cin_p, n->wt);
+        NN_CHECK(cudaGetLastError());
+        const ConvDims db{n->B, n->D, n->H, n->W, dm.cout_p, dm.cin_p};
+        NN_CHECK(run_conv<2>(gcur, n->wt, nullptr, gnext, n->act[l], db, s));
+        std::swap(gcur, gnext);
+    }
+    return KGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kgs_net_create(kgs_net **out, int n_layers, const int *channels, unsigned long long seed, void *stream)
+{
+    if (!out || n_layers < 1 || !channels) return KGS_EINVAL;
+    for (int l = 0; l <= n_layers; l++)
+        if (channels[l] < 1 || pad16(channels[l]) > 112) return KGS_EINVAL;
+    kgs_net *n = new (std::nothrow) kgs_net();
+    if (!n) return KGS_ENOMEM;
+    cudaGetDevice(&n->dev);
+    n->stream = static_cast<cudaStream_t>(stream);
+    n->L = n_layers;
+    for (int l = 0; l <= n_layers; l++) {
+        n->c.push_back(channels[l]);
+        n->cp.push_back(pad16(channels[l]));
+    }
+    size_t off = 0, wmax = 0;
+    for (int l = 0; l < n_layers; l++) {
+        n->w_off.push_back(off);
+        const size_t per = (size_t)27 * n->cp[l + 1] * n->cp[l];
+        wmax = std::max(wmax, per);
+        off += per;
+        n->b_off.push_back(off);
+        off += n->cp[l + 1];
+    }
+    n->n_params = off;
+    // He-normal initial weights over the real fan-in (Box-Muller on a
+    // splitmix64 stream), zero biases and zero padding
+    std::vector<float> h(off, 0.f);
+    unsigned long long st = seed;
+    auto next = [&]() {
+        st += 0x9E3779B97F4A7C15ULL;
+        unsigned long long z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z ^= z >> 31;
+        return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < n_layers; l++) {
+        const double sd = std::sqrt(2.0 / (27.0 * n->c[l])) * (l == n_layers - 1 ? 0.1 : 1.0);
+        for (int t = 0; t < 27; t++)
+            for (int co = 0; co < n->c[l + 1]; co++)
+                for (int ci = 0; ci < n->c[l]; ci++) {
+                    const double u1 = next(), u2 = next();
+                    const double z = std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+                    h[n->w_off[l] + ((size_t)t * n->cp[l + 1] + co) * n->cp[l] + ci] = (float)(sd * z);
+                }
+    }
+    auto fail = [&](int rc) {
+        kgs_net_destroy(n);
+        return rc;
+    };
+    if (cudaMalloc(&n->p, off * 4) != cudaSuccess || cudaMalloc(&n->g, off * 4) != cudaSuccess ||
+        cudaMalloc(&n->m1, off * 4) != cudaSuccess || cudaMalloc(&n->m2, off * 4) != cudaSuccess ||
+        cudaMalloc(&n->pb, off * 2) != cudaSuccess || cudaMalloc(&n->wt, wmax * 2) != cudaSuccess ||
+        cudaMallocHost(&n->h_loss, sizeof(float)) != cudaSuccess)
+        return fail(KGS_ENOMEM);
+    if (cudaMemcpy(n->p, h.data(), off * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(n->g, 0, off * 4) != cudaSuccess || cudaMemset(n->m1, 0, off * 4) != cudaSuccess ||
+        cudaMemset(n->m2, 0, off * 4) != cudaSuccess)
+        return fail(KGS_ECUDA);
+    to_bf16_kernel<<<nblk(off, 256), 256, 0, n->stream>>>(n->p, off, n->pb);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(n->stream) != cudaSuccess) return fail(KGS_ECUDA);
+    *out = n;
+    return KGS_OK;
+}
+
+int kgs_net_num_params(kgs_net *n, long long *real, long long *padded)
+{
+    if (!n) return KGS_EINVAL;
+    long long r = 0;
+    for (int l = 0; l < n->L; l++) r += 27LL * n->c[l] * n->c[l + 1] + n->c[l + 1];
+    if (real) *real = r;
+    if (padded) *padded = (long long)n->n_params;
+    return KGS_OK;
+}
+
+// Parameters in the unpadded layout: per layer W[27][cout][cin] then b[cout].
+static void pack_unpadded(const kgs_net *n, const float *padded, float *flat)
+{
+    size_t k = 0;
+    for (int l = 0; l < n->L; l++) {
+        for (int t = 0; t < 27; t++)
+            for (int co = 0; co < n->c[l + 1]; co++)
+                for (int ci = 0; ci < n->c[l]; ci++)
+                    flat[k++] = padded[n->w_off[l] + ((size_t)t * n->cp[l + 1] + co) * n->cp[l] + ci];
+        for (int co = 0; co < n->c[l + 1]; co++) flat[k++] = padded[n->b_off[l] + co];
+    }
+}
+
+static void unpack_unpadded(const kgs_net *n, const float *flat, float *padded)
+{
+    size_t k = 0;
+    for (int l = 0; l < n->L; l++) {
+        for (int t = 0; t < 27; t++)
+            for (int co = 0; co < n->c[l + 1]; co++)
+                for (int ci = 0; ci < n->c[l]; ci++)
+                    padded[n->w_off[l] + ((size_t)t * n->cp[l + 1] + co) * n->cp[l] + ci] = flat[k++];
+        for (int co = 0; co < n->c[l + 1]; co++) padded[n->b_off[l] + co] = flat[k++];
+    }
+}
+
+int kgs_net_get(kgs_net *n, int what, float *host)
+{
+    if (!n || !host || what < 0 || what > 1) return KGS_EINVAL;
+    std::vector<float> h(n->n_params);
+    NN_CHECK(cudaStreamSynchronize(n->stream));
+    NN_CHECK(cudaMemcpy(h.data(), what == 0 ? n->p : n->g, n->n_params * 4, cudaMemcpyDeviceToHost));
+    pack_unpadded(n, h.data(), host);
+    return KGS_OK;
+}
+
+int kgs_net_set_params(kgs_net *n, const float *host)
+{
+    if (!n || !host) return KGS_EINVAL;
+    std::vector<float> h(n->n_params, 0.f);
+    unpack_unpadded(n, host, h.data());
+    NN_CHECK(cudaMemcpy(n->p, h.data(), n->n_params * 4, cudaMemcpyHostToDevice));
+    to_bf16_kernel<<<nblk(n->n_params, 256), 256, 0, n->stream>>>(n->p, n->n_params, n->pb);
+    NN_CHECK(cudaGetLastError());
+    NN_CHECK(cudaMemset(n->m1, 0, n->n_params * 4));
+    NN_CHECK(cudaMemset(n->m2, 0, n->n_params * 4));
+    n->step = 0;
+    NN_CHECK(cudaStreamSynchronize(n->stream));
+    return KGS_OK;
+}
+
+int kgs_net_forward(kgs_net *n, const float *x, int B, int D, int H, int W, float *y)
+{
+    if (!n || !x || !y || B < 1 || D < 1 || H < 1 || W < 1) return KGS_EINVAL;
+    (void)cudaGetLastError();
+    int rc;
+    if ((rc = ensure_shape(n, B, D, H, W)) || (rc = forward(n, x))) return rc;
+    const size_t nvox = (size_t)B * D * H * W;
+    unpack_output_kernel<<<nblk(nvox * n->c[n->L], 256), 256, 0, n->stream>>>(n->out, nvox, n->cp[n->L],
+                                                                              n->c[n->L], y);
+    NN_CHECK(cudaGetLastError());
+    return KGS_OK;
+}
+
+int kgs_net_train_step(kgs_net *n, const float *x, const float *target, const uint8_t *mask, int B, int D, int H,
+                       int W, float lr, float *loss)
+{
+    if (!n || !x || !target || B < 1 || D < 1 || H < 1 || W < 1) return KGS_EINVAL;
+    (void)cudaGetLastError();
+    int rc;
+    if ((rc = ensure_shape(n, B, D, H, W)) || (rc = forward(n, x))) return rc;
+    const size_t nvox = (size_t)B * D * H * W;
+    const unsigned nb = nblk(nvox, 256);
+    if (nb > n->loss_part_cap) {
+        if (n->loss_part) cudaFree(n->loss_part);
+        n->loss_part = nullptr;
+        NN_CHECK(cudaMalloc(&n->loss_part, nb * sizeof(float)));
+        n->loss_part_cap = nb;
+    }
+    // masked voxel count on the host is not needed: the mask is a device
+    // array; count = voxels x channels when no mask is given, else the caller
+    // passes a mask whose count the loss normalises over (see below)
+    float count = (float)nvox;
+    if (mask) {
+        std::vector<uint8_t> hm(nvox);
+        NN_CHECK(cudaMemcpyAsync(hm.data(), mask, nvox, cudaMemcpyDeviceToHost, n->stream));
+        NN_CHECK(cudaStreamSynchronize(n->stream));
+        size_t k = 0;
+        for (uint8_t v : hm) k += v != 0;
+        count = (float)std::max<size_t>(k, 1);
+    }
+    const int cL = n->c[n->L], cpL = n->cp[n->L];
+    mse_kernel<<<nb, 256, 0, n->stream>>>(n->out, target, mask, nvox, cpL, cL, 1.f / (count * cL), n->ga,
+                                          n->loss_part);
+    NN_CHECK(cudaGetLastError());
+    if ((rc = backward(n))) return rc;
+    n->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
+    if (lr > 0.f) {
+        adam_kernel<<<nblk(n->n_params, 256), 256, 0, n->stream>>>(n->p, n->g, n->m1, n->m2, n->pb, n->n_params, lr,
+                                                                   b1, b2, 1e-8f, c1, c2);
+        NN_CHECK(cudaGetLastError());
+    }
+    if (loss) {
+        std::vector<float> hp(nb);
+        NN_CHECK(cudaMemcpyAsync(hp.data(), n->loss_part, nb * sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+        NN_CHECK(cudaStreamSynchronize(n->stream));
+        double s = 0.0;
+        for (float v : hp) s += v;
+        *loss = (float)(s / (count * cL));
+    }
+    return KGS_OK;
+}
+
+int kgs_surrogate_features(int nx, int ny, int nz, int nxc, int nyc, int nzc, const double *coarse,
+                           const uint8_t *solid, double kn, double u_lid, float *x, double *up, void *stream)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nxc < 1 || nyc < 1 || nzc < 1 || !coarse || !x || !up || !(kn > 0.0))
+        return KGS_EINVAL;
+    const size_t ncell = (size_t)nx * ny * nz;
+    features_kernel<<<nblk(ncell, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        nx, ny, nz, nxc, nyc, nzc, coarse, solid, (float)std::log(kn), (float)u_lid, x, up);
+    NN_CHECK(cudaGetLastError());
+    return KGS_OK;
+}
+
+int kgs_surrogate_target(long long ncell, const double *fine, const double *up, float *target, void *stream)
+{
+    if (ncell < 1 || !fine || !up || !target) return KGS_EINVAL;
+    target_kernel<<<nblk((size_t)ncell, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>((size_t)ncell, fine, up,
+                                                                                           target);
+    NN_CHECK(cudaGetLastError());
+    return KGS_OK;
+}
+
+int kgs_surrogate_apply(long long ncell, const double *up, const float *y, double *macros, int *n_bad, void *stream)
+{
+    if (ncell < 1 || !up || !y || !macros || !n_bad) return KGS_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *d_bad = nullptr;
+    NN_CHECK(cudaMallocAsync(reinterpret_cast<void **>(&d_bad), sizeof(int), st));
+    cudaError_t e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        apply_kernel<<<nblk((size_t)ncell, 256), 256, 0, st>>>((size_t)ncell, up, y, macros, d_bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d_bad, st);
+    return err(e);
+}
+
+void kgs_net_destroy(kgs_net *n)
+{
+    if (!n) return;
+    cudaStreamSynchronize(n->stream);
+    free_acts(n);
+    float *bufs[] = {n->p, n->g, n->m1, n->m2, n->wpart, n->loss_part};
+    for (float *b : bufs)
+        if (b) cudaFree(b);
+    if (n->pb) cudaFree(n->pb);
+    if (n->wt) cudaFree(n->wt);
+    if (n->h_loss) cudaFreeHost(n->h_loss);
+    delete n;
+}
+
+}  // extern "C"

@@ -415,3 +415,111 @@ def kgs_batch_destroy(b):
     if b.handle:
         load().kgs_batch_destroy(b.handle)
         b.handle = None
+
+
+# ---- learned initial guess (kgs_net_*, kgs_surrogate_*) ----
+_fp = ctypes.POINTER(ctypes.c_float)
+_vp = ctypes.c_void_p
+SIGNATURES.update({
+    "kgs_net_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.c_ulonglong, _vp]),
+    "kgs_net_num_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "kgs_net_get": (ctypes.c_int, [_vp, ctypes.c_int, _fp]),
+    "kgs_net_set_params": (ctypes.c_int, [_vp, _fp]),
+    "kgs_net_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
+    "kgs_net_train_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_float, _fp]),
+    "kgs_net_destroy": (None, [_vp]),
+    "kgs_surrogate_features": (ctypes.c_int, [ctypes.c_int] * 6 + [_vp, _vp, ctypes.c_double, ctypes.c_double,
+                                                                   _vp, _vp, _vp]),
+    "kgs_surrogate_target": (ctypes.c_int, [ctypes.c_longlong, _vp, _vp, _vp, _vp]),
+    "kgs_surrogate_apply": (ctypes.c_int, [ctypes.c_longlong, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int), _vp]),
+})
+
+
+class Net:
+    """Handle of one kgs_net; channels = (input, hidden..., output)."""
+
+    def __init__(self, handle, channels):
+        self.handle = handle
+        self.channels = tuple(channels)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            kgs_net_destroy(self)
+
+
+def _sp(stream):
+    return ctypes.c_void_p(stream) if stream else None
+
+
+def kgs_net_create(channels, seed=0, stream=None):
+    ch = (ctypes.c_int * len(channels))(*channels)
+    h = ctypes.c_void_p()
+    _check(load().kgs_net_create(ctypes.byref(h), len(channels) - 1, ch, int(seed), _sp(stream)), "kgs_net_create")
+    return Net(h, channels)
+
+
+def kgs_net_num_params(net):
+    r, p = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    _check(load().kgs_net_num_params(net.handle, ctypes.byref(r), ctypes.byref(p)), "kgs_net_num_params")
+    return r.value, p.value
+
+
+def kgs_net_get(net, what=0):
+    """Parameters (what=0) or gradients (what=1) as one float32 vector in the
+    host layout: per layer W[27][Cout][Cin] then b[Cout]."""
+    n, _ = kgs_net_num_params(net)
+    out = np.empty(n, np.float32)
+    _check(load().kgs_net_get(net.handle, int(what), out.ctypes.data_as(_fp)), "kgs_net_get")
+    return out
+
+
+def kgs_net_set_params(net, flat):
+    f = _arr(flat, np.float32)
+    return _check(load().kgs_net_set_params(net.handle, f.ctypes.data_as(_fp)), "kgs_net_set_params")
+
+
+def kgs_net_forward(net, x_ptr, shape, y_ptr):
+    """x_ptr, y_ptr: device addresses of [B][D][H][W][C] float32 tensors."""
+    B, D, H, W = shape
+    return _check(load().kgs_net_forward(net.handle, ctypes.c_void_p(x_ptr), B, D, H, W, ctypes.c_void_p(y_ptr)),
+                  "kgs_net_forward")
+
+
+def kgs_net_train_step(net, x_ptr, target_ptr, mask_ptr, shape, lr):
+    """One Adam step (lr <= 0: gradients only); returns the loss before it."""
+    B, D, H, W = shape
+    loss = ctypes.c_float(0.0)
+    _check(load().kgs_net_train_step(net.handle, ctypes.c_void_p(x_ptr), ctypes.c_void_p(target_ptr),
+                                     ctypes.c_void_p(mask_ptr) if mask_ptr else None, B, D, H, W,
+                                     float(lr), ctypes.byref(loss)), "kgs_net_train_step")
+    return loss.value
+
+
+def kgs_net_destroy(net):
+    if net.handle:
+        load().kgs_net_destroy(net.handle)
+        net.handle = None
+
+
+def kgs_surrogate_features(fine_shape, coarse_shape, coarse_ptr, solid_ptr, kn, u_lid, x_ptr, up_ptr, stream=None):
+    """fine_shape, coarse_shape: (nx, ny, nz)."""
+    return _check(load().kgs_surrogate_features(*fine_shape, *coarse_shape, ctypes.c_void_p(coarse_ptr),
+                                                ctypes.c_void_p(solid_ptr) if solid_ptr else None, float(kn),
+                                                float(u_lid), ctypes.c_void_p(x_ptr), ctypes.c_void_p(up_ptr),
+                                                _sp(stream)), "kgs_surrogate_features")
+
+
+def kgs_surrogate_target(ncell, fine_ptr, up_ptr, target_ptr, stream=None):
+    return _check(load().kgs_surrogate_target(int(ncell), ctypes.c_void_p(fine_ptr), ctypes.c_void_p(up_ptr),
+                                              ctypes.c_void_p(target_ptr), _sp(stream)), "kgs_surrogate_target")
+
+
+def kgs_surrogate_apply(ncell, up_ptr, y_ptr, macros_ptr, stream=None):
+    """Returns the number of cells whose guess is not a physical state."""
+    bad = ctypes.c_int(0)
+    _check(load().kgs_surrogate_apply(int(ncell), ctypes.c_void_p(up_ptr), ctypes.c_void_p(y_ptr),
+                                      ctypes.c_void_p(macros_ptr), ctypes.byref(bad), _sp(stream)),
+           "kgs_surrogate_apply")
+    return bad.value

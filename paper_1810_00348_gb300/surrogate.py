@@ -1,0 +1,212 @@
+"""Learned initial guess for the iterative solver: training data from the
+solver itself, training, inference, and the uniform-start fallback.
+
+The paper starts each solve from a uniform state and observes that the
+iteration needs many steps at small Knudsen number (Section 4.1).  Here a
+solve of a cavity starts instead from a guess: the converged solution of the
+same problem on a grid twice as coarse, upsampled trilinearly, plus a
+correction predicted by a 3D convolutional network (about one million
+parameters, channels 11-48-112-112-112-48-8) from (log Kn, lid speed, solid
+flag, upsampled coarse fields).  A guess that is not a physical state (a
+non-finite value, rho <= 0 or T <= 0 anywhere) is rejected and the solve
+starts from the uniform state.
+
+Every numeric step runs in libkgs's CUDA kernels (kgs_batch_* for the
+solves, kgs_surrogate_* for the feature and guess maps, kgs_net_* for the
+network); this module orders those calls and keeps the device buffers
+(torch tensors) between them.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import inputs, kgs
+
+DEFAULT_CHANNELS = (11, 48, 112, 112, 112, 48, 8)
+N_FEATURES = 11
+N_FIELDS = 8
+
+
+def lid_speed(prob: inputs.Problem) -> float:
+    """Largest wall speed of the problem (the lid of a cavity)."""
+    return max(math.sqrt(sum(u * u for u in uw)) for uw in prob.U_w)
+
+
+def coarse_problem(prob: inputs.Problem, factor: int = 2) -> inputs.Problem:
+    """The same problem on cells `factor` times wider in each direction (the
+    velocity grid, gas and boundaries unchanged).  Needs equal-width cells,
+    extents divisible by `factor` and no solid cells."""
+    if prob.solid is not None:
+        raise ValueError("coarse_problem: problems with solid cells are not supported")
+    dims = (prob.nx, prob.ny, prob.nz)
+    if any(n % factor for n in dims):
+        raise ValueError("coarse_problem: extents %s not divisible by %d" % (dims, factor))
+    for d in (prob.dx, prob.dy, prob.dz):
+        if not np.allclose(d, d[0], rtol=1e-12, atol=0.0):
+            raise ValueError("coarse_problem: cells must have equal widths")
+    nx, ny, nz = (n // factor for n in dims)
+    return dataclasses.replace(prob, nx=nx, ny=ny, nz=nz, dx=np.full(nx, prob.dx[0] * factor),
+                               dy=np.full(ny, prob.dy[0] * factor), dz=np.full(nz, prob.dz[0] * factor),
+                               name=prob.name + " (coarse /%d)" % factor)
+
+
+def solve(probs: Sequence[inputs.Problem], precision=kgs.KGS_MIXED, tol=1e-6, max_iters=5000,
+          initial: Optional[Sequence[Optional[np.ndarray]]] = None):
+    """Solve a batch of problems to `tol` in one kgs_batch.  Returns (list of
+    macroscopic fields [8, nz, ny, nx], iterations per problem, residuals,
+    status code)."""
+    b = kgs.kgs_batch_setup(list(probs), precision=precision, tol=tol, max_iters=max_iters)
+    if initial is not None:
+        for i, m in enumerate(initial):
+            if m is not None:
+                kgs.kgs_batch_set_initial(b, i, m)
+    rc, done, res = kgs.kgs_batch_iterate(b, 0)
+    out = [kgs.kgs_batch_moments(b, i) for i in range(len(probs))]
+    kgs.kgs_batch_destroy(b)
+    return out, done, res, rc
+
+
+def upsample(prob: inputs.Problem, coarse: np.ndarray, kn: Optional[float] = None):
+    """Features x [nz, ny, nx, 11] (float32) and the upsampled coarse fields
+    up [8, nz, ny, nx] (float64), both device tensors."""
+    cz, cy, cx = coarse.shape[1:]
+    x = torch.empty((prob.nz, prob.ny, prob.nx, N_FEATURES), dtype=torch.float32, device="cuda")
+    up = torch.empty((N_FIELDS, prob.nz, prob.ny, prob.nx), dtype=torch.float64, device="cuda")
+    cd = torch.as_tensor(np.ascontiguousarray(coarse), dtype=torch.float64, device="cuda")
+    sd = None
+    if prob.solid is not None:
+        sd = torch.as_tensor(np.ascontiguousarray(prob.solid), dtype=torch.uint8, device="cuda")
+    kgs.kgs_surrogate_features((prob.nx, prob.ny, prob.nz), (cx, cy, cz), cd.data_ptr(),
+                               sd.data_ptr() if sd is not None else None, prob.Kn if kn is None else kn,
+                               lid_speed(prob), x.data_ptr(), up.data_ptr(),
+                               torch.cuda.current_stream().cuda_stream)
+    return x, up
+
+
+@dataclasses.dataclass
+class Sample:
+    prob: inputs.Problem
+    coarse: np.ndarray       # converged coarse-grid fields [8, nz/2, ny/2, nx/2]
+    fine: np.ndarray         # converged fields [8, nz, ny, nx]
+    iters_coarse: int
+    iters_fine: int
+
+
+def draw_cavities(n: int, seed: int, cells: int, vels: int, kn_range=(0.05, 0.5), lid_range=(0.05, 0.3),
+                  L_v: float = 4.0) -> List[inputs.Problem]:
+    """Cavities of one size: Kn log-uniform and lid speed uniform on the given
+    ranges, drawn from splitmix64(seed)."""
+    g = inputs.SplitMix64(seed)
+    out = []
+    for _ in range(n):
+        kn = kn_range[0] * (kn_range[1] / kn_range[0]) ** g.uniform()
+        lid = lid_range[0] + (lid_range[1] - lid_range[0]) * g.uniform()
+        out.append(inputs.cavity(cells, vels, Kn=kn, lid=lid, L_v=L_v))
+    return out
+
+
+def make_samples(probs: Sequence[inputs.Problem], precision=kgs.KGS_MIXED, tol=1e-6, max_iters=5000,
+                 factor: int = 2) -> List[Sample]:
+    """Converged coarse and fine solutions of each problem; the fine solves
+    start from the upsampled coarse solutions (only the converged fields are
+    kept, so the start changes nothing but the time taken)."""
+    coarse_probs = [coarse_problem(p, factor) for p in probs]
+    coarse, it_c, _, _ = solve(coarse_probs, precision, tol, max_iters)
+    starts = []
+    for p, c in zip(probs, coarse):
+        _, up = upsample(p, c)
+        starts.append(up.cpu().numpy())
+    fine, it_f, _, _ = solve(probs, precision, tol, max_iters, initial=starts)
+    return [Sample(p, c, f, ic, jf) for p, c, f, ic, jf in zip(probs, coarse, fine, it_c, it_f)]
+
+
+class Surrogate:
+    """A kgs_net with the feature and guess maps around it."""
+
+    def __init__(self, channels=DEFAULT_CHANNELS, seed: int = 0):
+        if channels[0] != N_FEATURES or channels[-1] != N_FIELDS:
+            raise ValueError("the network maps %d features to %d fields" % (N_FEATURES, N_FIELDS))
+        self.channels = tuple(channels)
+        self.net = kgs.kgs_net_create(self.channels, seed=seed,
+                                      stream=torch.cuda.current_stream().cuda_stream)
+
+    def num_params(self) -> int:
+        return kgs.kgs_net_num_params(self.net)[0]
+
+    def train(self, samples: Sequence[Sample], steps: int, batch: int = 8, lr: float = 1e-3, seed: int = 0,
+              lr_final: Optional[float] = None) -> List[float]:
+        """Adam on the mean squared error of the normalised correction, on
+        mini-batches drawn without replacement from a seeded permutation;
+        the step size decays by cosine to lr_final (default lr / 20).
+        All samples must share one grid.  Returns the loss per step."""
+        shape = (samples[0].prob.nz, samples[0].prob.ny, samples[0].prob.nx)
+        if any((s.prob.nz, s.prob.ny, s.prob.nx) != shape for s in samples):
+            raise ValueError("train: samples must share one grid")
+        ncell = int(np.prod(shape))
+        X = torch.empty((len(samples),) + shape + (N_FEATURES,), dtype=torch.float32, device="cuda")
+        T = torch.empty((len(samples), ncell, N_FIELDS), dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream().cuda_stream
+        for i, s in enumerate(samples):
+            x, up = upsample(s.prob, s.coarse)
+            X[i].copy_(x)
+            fd = torch.as_tensor(np.ascontiguousarray(s.fine), dtype=torch.float64, device="cuda")
+            kgs.kgs_surrogate_target(ncell, fd.data_ptr(), up.data_ptr(), T[i].data_ptr(), stream)
+        batch = min(batch, len(samples))
+        xb = torch.empty((batch,) + X.shape[1:], dtype=X.dtype, device="cuda")
+        tb = torch.empty((batch,) + T.shape[1:], dtype=T.dtype, device="cuda")
+        rng = np.random.default_rng(seed)
+        lr_final = lr / 20 if lr_final is None else lr_final
+        order, pos, losses = rng.permutation(len(samples)), 0, []
+        for step in range(steps):
+            if pos + batch > len(order):
+                order, pos = rng.permutation(len(samples)), 0
+            idx = torch.as_tensor(order[pos:pos + batch], device="cuda")
+            pos += batch
+            torch.index_select(X, 0, idx, out=xb)
+            torch.index_select(T, 0, idx, out=tb)
+            lr_t = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * step / max(steps, 1)))
+            losses.append(kgs.kgs_net_train_step(self.net, xb.data_ptr(), tb.data_ptr(), None, (batch,) + shape,
+                                                 lr_t))
+        return losses
+
+    def guess(self, prob: inputs.Problem, coarse: np.ndarray):
+        """Initial fields [8, nz, ny, nx] (host) for `prob` from its coarse
+        solution, or None when the guess is rejected (the caller then starts
+        from the uniform state), and the number of cells that failed the check."""
+        x, up = upsample(prob, coarse)
+        y = torch.empty((prob.ncell, N_FIELDS), dtype=torch.float32, device="cuda")
+        kgs.kgs_net_forward(self.net, x.data_ptr(), (1, prob.nz, prob.ny, prob.nx), y.data_ptr())
+        m = torch.empty_like(up)
+        n_bad = kgs.kgs_surrogate_apply(prob.ncell, up.data_ptr(), y.data_ptr(), m.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream)
+        if n_bad:
+            return None, n_bad
+        return m.cpu().numpy(), 0
+
+    def predict(self, prob: inputs.Problem, coarse: np.ndarray) -> np.ndarray:
+        """Raw network output for prob: normalised correction [nz, ny, nx, 8]."""
+        x, _ = upsample(prob, coarse)
+        y = torch.empty((prob.ncell, N_FIELDS), dtype=torch.float32, device="cuda")
+        kgs.kgs_net_forward(self.net, x.data_ptr(), (1, prob.nz, prob.ny, prob.nx), y.data_ptr())
+        return y.cpu().numpy().reshape(prob.nz, prob.ny, prob.nx, N_FIELDS)
+
+
+def iterations_to(prob: inputs.Problem, initial: Optional[np.ndarray], precision=kgs.KGS_MIXED, tol=1e-6,
+                  max_iters=5000):
+    """(iterations, seconds, residual, status) of one solve from `initial`
+    (None = uniform state), timed around kgs_iterate."""
+    ctx = kgs.kgs_setup(prob, precision=precision, tol=tol, max_iters=max_iters)
+    kgs.kgs_set_initial(ctx, initial)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, n, res = kgs.kgs_iterate(ctx, 0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    kgs.kgs_destroy(ctx)
+    return n, dt, res, rc
