@@ -83,21 +83,8 @@ int build_items(kgs_batch *b)
     for (int i = 0; i < b->n; i++)
         if (b->active[i]) max_stage = std::max(max_stage, (int)b->ctx[i]->t.stage_n.size());
     for (int s = 0; s < max_stage; s++)
-        for (int i = 0; i < b->n; i++) {
-            if (!b->active[i]) continue;
-            const HostTables &t = b->ctx[i]->t;
-            for (int o = 0; o < 8; o++) {
-                const int ng = (t.oct_vcount[o] + t.vg_size - 1) / t.vg_size;
-                for (int vg = 0; vg < ng; vg++)
-                    for (int bzr = 0; bzr < t.nbz; bzr++)
-                        for (int byr = 0; byr < t.nby; byr++) {
-                            const int bxr = s - bzr - byr;
-                            if (bxr < 0 || bxr >= t.nbx) continue;
-                            items.push_back(
-                                make_int4(i, (o << 24) | vg, bxr | (byr << 10) | (bzr << 20), t.oct_vgbase[o] + vg));
-                        }
-            }
-        }
+        for (int i = 0; i < b->n; i++)
+            if (b->active[i]) ctx_stage_items(b->ctx[i]->t, i, s, items);
     b->n_items = (int)items.size();
     if (items.size() > b->items_cap) {
         if (b->d_items) cudaFree(b->d_items);

@@ -34,7 +34,17 @@ struct kgs_ctx {
     int *d_vstart = nullptr, *d_vcount = nullptr, *d_vgbase = nullptr, *d_vg_oct = nullptr;
     double *blk_mass = nullptr, *blk_res = nullptr, *scale = nullptr, *resid = nullptr;
     int *blk_bad = nullptr;
-    double *h_resid = nullptr;  // pinned
+    double *h_resid = nullptr;  // pinned: residual, divergence flag, wait-error word
+    // persistent sweep of a standalone context: one launch per iteration over
+    // the work items in stage order; a CTA waits (bounded) for the three
+    // upwind blocks of its item.  Not set up for the instances of a batch.
+    int persist = 0;
+    int persist_grid = 0, persist_items = 0;
+    int4 *p_items = nullptr;
+    int *p_counter = nullptr, *p_flags = nullptr, *p_flag_off = nullptr;
+    size_t p_n_flags = 0;
+    kgs::SweepArgs *p_args = nullptr, *h_args = nullptr;  // device copy, pinned host staging
+    long long spin_limit = 20000000;  // polls of ~100 ns before a wait gives up
     size_t device_bytes = 0;
     std::vector<void *> allocs;
     // profiling
@@ -54,6 +64,12 @@ int ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const 
                const kgs_bc *bc, const kgs_opts *opts);
 void ctx_free(kgs_ctx *c);
 SweepArgs ctx_sweep_args(const kgs_ctx *c);
+// Work items of instance `inst` at wavefront stage `stage`, appended in the
+// order the persistent sweep claims them: (inst, octant << 24 | group,
+// reflected block coordinates packed 10 bits each, global group index).
+void ctx_stage_items(const HostTables &t, int inst, int stage, std::vector<int4> &out);
+// Set up the persistent sweep of a standalone context (items, flags, grid).
+int ctx_persist_init(kgs_ctx *c);
 // Phases of one outer iteration (asynchronous on the context's stream).
 int ctx_launch_coef(kgs_ctx *c);
 int ctx_launch_stages(kgs_ctx *c);

@@ -88,6 +88,8 @@ void free_all(kgs_ctx *c)
     c->ev.clear();
     if (c->h_resid) cudaFreeHost(c->h_resid);
     c->h_resid = nullptr;
+    if (c->h_args) cudaFreeHost(c->h_args);
+    c->h_args = nullptr;
 }
 
 // Upload macros (or the uniform state), set M0 and the wall densities from
@@ -184,6 +186,30 @@ int kgs::ctx_launch_stages(kgs_ctx *c)
     const HostTables &t = c->t;
     cudaStream_t st = c->stream;
     SweepArgs a = ctx_sweep_args(c);
+    if (c->persist) {
+        // the previous iteration has completed (run_iteration synchronises),
+        // so the pinned staging copy is free to be rewritten
+        *c->h_args = a;
+        KGS_CHECK(cudaMemcpyAsync(c->p_args, c->h_args, sizeof(SweepArgs), cudaMemcpyHostToDevice, st));
+        KGS_CHECK(cudaMemsetAsync(c->p_counter, 0, sizeof(int), st));
+        KGS_CHECK(cudaMemsetAsync(c->p_flags, 0, c->p_n_flags * sizeof(int), st));
+        BatchSweepArgs ba;
+        ba.inst = c->p_args;
+        ba.items = c->p_items;
+        ba.n_items = c->persist_items;
+        ba.counter = c->p_counter;
+        ba.flags = c->p_flags;
+        ba.flag_off = c->p_flag_off;
+        ba.error = reinterpret_cast<int *>(c->resid + 2);
+        ba.spin_limit = c->spin_limit;
+        ba.skip_publish = -1;
+        if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[0], st));
+        KGS_CHECK(launch_sweep_persistent(t.precision, t.tv, a.line16, ba, t.nxo_max, c->persist_grid, st));
+        if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[1], st));
+        c->kernel_launches += 1;
+        c->sweep_launches += 1;
+        return KGS_OK;
+    }
     const int ns = (int)t.stage_n.size();
     for (int s = 0; s < ns; s++) {
         a.work = c->work + t.stage_off[s];
@@ -193,6 +219,44 @@ int kgs::ctx_launch_stages(kgs_ctx *c)
     }
     c->kernel_launches += ns;
     c->sweep_launches += ns;
+    return KGS_OK;
+}
+
+void kgs::ctx_stage_items(const HostTables &t, int inst, int stage, std::vector<int4> &out)
+{
+    for (int o = 0; o < 8; o++) {
+        const int ng = (t.oct_vcount[o] + t.vg_size - 1) / t.vg_size;
+        for (int vg = 0; vg < ng; vg++)
+            for (int bzr = 0; bzr < t.nbz; bzr++)
+                for (int byr = 0; byr < t.nby; byr++) {
+                    const int bxr = stage - bzr - byr;
+                    if (bxr < 0 || bxr >= t.nbx) continue;
+                    out.push_back(make_int4(inst, (o << 24) | vg, bxr | (byr << 10) | (bzr << 20), t.oct_vgbase[o] + vg));
+                }
+    }
+}
+
+int kgs::ctx_persist_init(kgs_ctx *c)
+{
+    const HostTables &t = c->t;
+    int sms = 0;
+    KGS_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+    const int line16 = ctx_sweep_args(c).line16;
+    const int per_sm =
+        sweep_persistent_occupancy(t.precision, t.tv, line16, sweep_smem_bytes(t.precision, t.tv, t.nxo_max));
+    if (per_sm < 1) return KGS_OK;  // keep the launch per stage
+    std::vector<int4> items;
+    for (int s = 0; s < (int)t.stage_n.size(); s++) ctx_stage_items(t, 0, s, items);
+    int rc;
+    c->p_n_flags = (size_t)t.n_vg * t.nbx * t.nby * t.nbz;
+    if ((rc = upload(c, &c->p_items, items)) || (rc = dalloc_t(c, &c->p_counter, 1)) ||
+        (rc = dalloc_t(c, &c->p_flags, c->p_n_flags)) || (rc = upload(c, &c->p_flag_off, std::vector<int>(1, 0))) ||
+        (rc = dalloc_t(c, &c->p_args, 1)))
+        return rc;
+    KGS_CHECK(cudaMallocHost(&c->h_args, sizeof(SweepArgs)));
+    c->persist_items = (int)items.size();
+    c->persist_grid = sms * per_sm;
+    c->persist = 1;
     return KGS_OK;
 }
 
@@ -244,10 +308,18 @@ int run_iteration(kgs_ctx *c, double *residual, int *bad)
     int rc;
     if ((rc = ctx_launch_coef(c)) || (rc = ctx_launch_stages(c)) || (rc = ctx_launch_closure(c, c->resid)))
         return rc;
-    KGS_CHECK(cudaMemcpyAsync(c->h_resid, c->resid, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    KGS_CHECK(cudaMemcpyAsync(c->h_resid, c->resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
+    if (c->persist && *reinterpret_cast<const int *>(c->h_resid + 2) != 0) {
+        // a bounded wait of the persistent sweep gave up: clear the word and
+        // report; the iteration's results are not used
+        KGS_CHECK(cudaMemsetAsync(c->resid + 2, 0, sizeof(double), c->stream));
+        KGS_CHECK(cudaStreamSynchronize(c->stream));
+        return KGS_ETIMEOUT;
+    }
     if (c->profiling) {
-        for (size_t s = 0; s < c->t.stage_n.size(); s++) {
+        const size_t n_pairs = c->persist ? 1 : c->t.stage_n.size();
+        for (size_t s = 0; s < n_pairs; s++) {
             float ms = 0.f;
             KGS_CHECK(cudaEventElapsedTime(&ms, c->ev[2 * s], c->ev[2 * s + 1]));
             c->sweep_ms += ms;
@@ -287,7 +359,12 @@ int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const k
                               opts->block_z);
     if (rc) return rc;
     (void)cudaGetLastError();  // launches below check their own status
-    return ctx_create(out, grid, solid, vg, gas, bc, opts);
+    if ((rc = ctx_create(out, grid, solid, vg, gas, bc, opts))) return rc;
+    if ((rc = ctx_persist_init(*out))) {
+        kgs_destroy(*out);
+        *out = nullptr;
+    }
+    return rc;
 }
 
 }  // extern "C"
@@ -333,7 +410,7 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
         (rc = upload(c, &c->d_vg_oct, t.vg_oct)) || (rc = dalloc_t(c, &c->blk_mass, close_blocks(n))) ||
         (rc = dalloc_t(c, &c->blk_res, (size_t)c->n_red_blocks * 10)) ||
         (rc = dalloc_t(c, &c->blk_bad, c->n_red_blocks)) || (rc = dalloc_t(c, &c->scale, 2)) ||
-        (rc = dalloc_t(c, &c->resid, 2)))
+        (rc = dalloc_t(c, &c->resid, 3)))
         return fail(rc);
     if (t.precision == KGS_FP64) {
         if ((rc = upload(c, reinterpret_cast<double **>(&c->velm), t.velm64))) return fail(rc);
@@ -346,7 +423,8 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
         cudaMemset(c->FZ, 0, (size_t)t.ny * t.nx * t.Nv * rsz) != cudaSuccess ||
         cudaMemset(c->coef, 0, n * NCOEF * rsz) != cudaSuccess)
         return fail(KGS_ECUDA);
-    if (cudaMallocHost(&c->h_resid, 2 * sizeof(double)) != cudaSuccess) return fail(KGS_ENOMEM);
+    if (cudaMallocHost(&c->h_resid, 3 * sizeof(double)) != cudaSuccess) return fail(KGS_ENOMEM);
+    if (cudaMemset(c->resid, 0, 3 * sizeof(double)) != cudaSuccess) return fail(KGS_ECUDA);
     c->ev.resize(2 * t.stage_n.size());
     for (auto &e : c->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(KGS_ECUDA);

@@ -357,7 +357,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         }
         __syncthreads();
         // c_x = xi_x - U_x of each cell of the slice as a float pair, per x node
-        {
+        // (lines of LINE nodes keep theirs in registers instead)
+        if constexpr (LINE == 0) {
             const int cl = t % SLICE, vp = t / SLICE;
             const Real ux = cs[cl * NCOEF + C_UX];
             for (int ix = vp; ix < nxo; ix += NT / SLICE) {
