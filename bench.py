@@ -37,6 +37,11 @@ N_CELL, N_VEL, KN, LID = 64, 32, 1.0, 0.16
 # (FMA = 2): equilibrium of Eq. (2) 20 + exp 1; implicit update of Eq. (7)
 # 13 (with the division); 13 moment sums about U^n 34.
 FLOPS_PER_PP = 68
+# dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch (ncu, 32^3
+# cells x 32^3 velocities, 256 velocities per CTA, blocks 8x8x32): 2.143e9 B
+# over 1.074e9 phase points
+TRAFFIC_BYTES_PER_PP = 2.143e9 / 1.074e9
+TRAFFIC_SHAPE = (256, 32)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of the GB300
@@ -211,9 +216,14 @@ def run_ours(args, world, rank, local):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = FLOPS_PER_PP * pp / (sweep_ms_iter / 1e3) / 1e12
+    # DRAM bytes per launch from an ncu capture of this kernel at 32^3 cells x
+    # 32^3 velocities with the same sweep shape, scaled by phase points
+    traffic = None
+    if (info["v_per_cta"], info["block_z"]) == TRAFFIC_SHAPE:
+        traffic = TRAFFIC_BYTES_PER_PP * pp
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "kernel": "sweep_kernel<float>", "flops_per_phase_point": FLOPS_PER_PP,
+                "frac": achieved / fp32_peak, "traffic": traffic,
+                "kernel": "sweep_persistent_kernel<float>", "flops_per_phase_point": FLOPS_PER_PP,
                 "peak_basis": "FP32 FMA lanes: %d SMs x %d lanes x 2 x %.0f MHz (derived)" % (
                     SM_COUNT, FP32_LANES_PER_SM, sm_mhz),
                 "sweep_ms_per_step": sweep_ms_iter, "sweep_share_of_step": sweep_ms_iter / ms_step}
@@ -254,6 +264,8 @@ def run_ours(args, world, rank, local):
     extras = {}
     if not args.no_extras:
         extras = run_extras(args, kgs, inputs, torch, peaks)
+        if not args.no_surrogate:
+            extras["surrogate"] = run_surrogate(args, kgs, inputs, torch, peaks)
 
     if rank != 0:
         return
@@ -344,6 +356,94 @@ def run_extras(args, kgs, inputs, torch, peaks):
     return out
 
 
+def run_surrogate(args, kgs, inputs, torch, peaks):
+    """The learned initial guess: tensor-core throughput of the network's
+    forward pass at 128^3 voxels and of a training step, then the time to a
+    residual of 1e-6 on held-out cavities from the uniform state (FP64, and
+    mixed then FP64) and from the network's guess (coarse solve, inference and
+    fine solve all counted)."""
+    import numpy as np
+
+    from paper_1810_00348_gb300 import surrogate
+    out = {}
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    ch = surrogate.DEFAULT_CHANNELS
+    flops_per_voxel = 2.0 * 27 * sum(a * b for a, b in zip(ch[:-1], ch[1:]))
+    s = surrogate.Surrogate(seed=0)
+
+    def ev_time(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    try:
+        shape = (1, 128, 128, 128)
+        x = torch.randn(shape + (surrogate.N_FEATURES,), device="cuda")
+        y = torch.empty(shape + (surrogate.N_FIELDS,), device="cuda")
+        ms = ev_time(lambda: kgs.kgs_net_forward(s.net, x.data_ptr(), shape, y.data_ptr()), 5)
+        tf = flops_per_voxel * np.prod(shape) / (ms / 1e3) / 1e12
+        out["inference"] = {"workload": "forward pass, 1 x 128^3 voxels, channels %s" % "-".join(map(str, ch)),
+                            "ms": ms, "tflops": tf,
+                            "roofline": {"bound": "tensor", "achieved": tf, "peak": bf16_peak, "unit": "TFLOP/s",
+                                         "frac": tf / bf16_peak, "peak_basis": "measured bf16 GEMM burst"}}
+        shape = (8, 32, 32, 32)
+        x = torch.randn(shape + (surrogate.N_FEATURES,), device="cuda")
+        t = torch.randn(shape + (surrogate.N_FIELDS,), device="cuda")
+        ms = ev_time(lambda: kgs.kgs_net_train_step(s.net, x.data_ptr(), t.data_ptr(), None, shape, 1e-5), 3)
+        tf = 3 * flops_per_voxel * np.prod(shape) / (ms / 1e3) / 1e12
+        out["training_step"] = {"workload": "forward + backward + Adam, 8 x 32^3 voxels", "ms": ms, "tflops": tf,
+                                "roofline_frac": tf / bf16_peak}
+        del x, t, y
+    except Exception as e:  # noqa: BLE001
+        out["throughput_error"] = repr(e)
+    try:
+        cells, vels, tol = args.surrogate_cells, 16, 1e-6
+        t0 = time.perf_counter()
+        train = surrogate.draw_cavities(args.surrogate_train, seed=1, cells=cells, vels=vels)
+        samples = surrogate.make_samples(train, precision=kgs.KGS_FP64, tol=tol, max_iters=5000)
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        losses = s.train(samples, steps=400, batch=8, lr=1e-3, seed=0)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        cases = []
+        for p in surrogate.draw_cavities(4, seed=2, cells=cells, vels=vels):
+            n_fp64, t_fp64, r_fp64, _ = surrogate.iterations_to(p, None, kgs.KGS_FP64, tol, 5000)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc_m, _, nm, nd, r_m = kgs.kgs_solve(p, None, tol, 5000)
+            t_mixed = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            rc_c, coarse, cm, cd, _ = kgs.kgs_solve(surrogate.coarse_problem(p), None, tol, 5000)
+            guess, n_bad = s.guess(p, coarse)
+            rc_s, _, sm, sd, r_s = kgs.kgs_solve(p, guess, tol, 5000)
+            torch.cuda.synchronize()
+            t_sur = time.perf_counter() - t0
+            cases.append({"Kn": p.Kn, "lid": surrogate.lid_speed(p),
+                          "fp64_uniform": {"iterations": n_fp64, "s": t_fp64, "residual": r_fp64},
+                          "mixed_fp64_uniform": {"iterations": [nm, nd], "s": t_mixed, "residual": r_m},
+                          "mixed_fp64_surrogate": {"iterations": [sm, sd], "coarse_iterations": [cm, cd],
+                                                   "s": t_sur, "residual": r_s, "guess_rejected": guess is None}})
+        out["time_to_1e-6"] = {
+            "workload": "held-out lid-driven cavities (splitmix64 seed 2): %d^3 cells x %d^3 velocities, "
+                        "Kn log-uniform [0.05,0.5], lid U[0.05,0.3]; coarse grid %d^3" % (cells, vels, cells // 2),
+            "training": {"samples": len(samples), "steps": 400, "batch": 8, "data_s": t_data, "train_s": t_train,
+                         "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:]))},
+            "cases": cases,
+            "speedup_vs_fp64": float(np.mean([c["fp64_uniform"]["s"] / c["mixed_fp64_surrogate"]["s"]
+                                              for c in cases])),
+        }
+    except Exception as e:  # noqa: BLE001
+        out["time_to_1e-6"] = {"error": repr(e)}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,6 +456,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and cube workloads")
     ap.add_argument("--batch-iters", type=int, default=20)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-initial-guess measurements")
+    ap.add_argument("--surrogate-cells", type=int, default=16, help="cells per side of the gain cavities")
+    ap.add_argument("--surrogate-train", type=int, default=48, help="training cavities")
     ap.add_argument("--cells", type=int, default=N_CELL, help="cells per side (profiling runs only)")
     ap.add_argument("--vels", type=int, default=N_VEL, help="velocities per side (profiling runs only)")
     args = ap.parse_args()

@@ -266,6 +266,22 @@ int kgs_batch_profile(kgs_batch *b, double *sweep_ms, long long *sweeps, long lo
 int kgs_batch_fault(kgs_batch *b, long long spin_limit, int unpublished_item);
 void kgs_batch_destroy(kgs_batch *b);
 
+/* ---- solve to a tolerance: mixed precision, then FP64 ----
+ * The FP32 form of the iteration settles into rounding noise around its
+ * fixed point, so its residual stops falling at a floor (about 3e-5 on the
+ * cavity's spanwise momentum).  kgs_solve runs mixed iterations in chunks of
+ * 5 while the residual keeps falling (below 0.9 x its best value within
+ * two chunks), then continues in FP64 from the mixed state (macros, wall
+ * densities and mass target carried over as by kgs_save / kgs_load) until
+ * the residual is below tol or max_iters iterations ran in all.
+ * initial: host [8][nz][ny][nx] or NULL (uniform state).  macros_out: host,
+ * caller-owned, [8][nz][ny][nx], may be NULL.  iters_mixed, iters_fp64,
+ * residual: host, may be NULL.  Allocates two contexts on `stream` for the
+ * duration of the call.  Returns KGS_OK, KGS_NOTCONVERGED, or the errors of
+ * kgs_setup / kgs_iterate. */
+int kgs_solve(const kgs_problem *prob, const double *initial, double tol, int max_iters, double *macros_out,
+              int *iters_mixed, int *iters_fp64, double *residual, void *stream);
+
 /* ---- learned initial guess ----
  * The paper starts every solve from a uniform state and notes that the
  * iteration converges slowly at small Knudsen number (Section 4.1); this

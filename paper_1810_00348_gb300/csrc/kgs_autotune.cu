@@ -75,6 +75,11 @@ int time_shape(const kgs_problem *p, int precision, int vpc, int bz, double *ms)
     kgs_ctx *c = nullptr;
     int rc = ctx_create(&c, &p->grid, p->solid, &p->vgrid, &p->gas, &p->bc, &o);
     if (rc) return rc;
+    if ((rc = ctx_persist_init(c))) {  // time the sweep that contexts and batches run
+        ctx_free(c);
+        delete c;
+        return rc;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const int timed = 2;
     auto one = [&]() -> int {

@@ -1,0 +1,91 @@
+// kgs_solve.cu -- a solve to a tolerance that runs the mixed-precision
+// iteration while it makes progress and finishes in FP64.
+//
+// The outer iteration of Eq. (6) is a contraction, so its FP32 form settles
+// into a band of rounding noise around its fixed point instead of reaching
+// it; the residual (relative L2 change per iteration, Section 4.1) then stops
+// falling at a floor set by the smallest field (about 3e-5 for the cavity's
+// spanwise momentum).  The FP64 iteration started from that state needs few
+// iterations to reach a tighter tolerance because the state is already within
+// the noise band of the fixed point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kgs_ctx.h"
+
+namespace {
+
+constexpr int CHUNK = 5;          // mixed iterations between progress checks
+constexpr int PATIENCE = 2;       // checks without progress before the switch
+constexpr double PROGRESS = 0.9;  // progress: residual below 0.9 x the best so far
+
+kgs_opts opts_for(const kgs_problem *p, int precision, double tol, int max_iters, void *stream)
+{
+    kgs_opts o{};
+    o.precision = precision;
+    o.wall_norm = p->wall_norm;
+    o.mass_rescale = p->mass_rescale;
+    o.max_iters = max_iters;
+    o.tol = tol;
+    o.stream = stream;
+    return o;
+}
+
+}  // namespace
+
+extern "C" int kgs_solve(const kgs_problem *p, const double *initial, double tol, int max_iters, double *macros_out,
+                         int *iters_mixed, int *iters_fp64, double *residual, void *stream)
+{
+    if (!p || !(tol > 0.0) || max_iters < 1) return KGS_EINVAL;
+    int n_mixed = 0, n_fp64 = 0, rc;
+    double r = -1.0;
+    kgs_ctx *m = nullptr, *d = nullptr;
+    std::vector<unsigned char> state;
+    auto finish = [&](int code) {
+        if (m) kgs_destroy(m);
+        if (d) kgs_destroy(d);
+        if (iters_mixed) *iters_mixed = n_mixed;
+        if (iters_fp64) *iters_fp64 = n_fp64;
+        if (residual) *residual = r;
+        return code;
+    };
+    kgs_opts om = opts_for(p, KGS_MIXED, tol, max_iters, stream);
+    if ((rc = kgs_setup(&m, &p->grid, p->solid, &p->vgrid, &p->gas, &p->bc, &om))) return finish(rc);
+    if (initial && (rc = kgs_set_initial(m, initial))) return finish(rc);
+    // mixed phase
+    double best = 1e300;
+    int stalled = 0;
+    while (n_mixed < max_iters) {
+        int done = 0;
+        rc = kgs_iterate(m, std::min(CHUNK, max_iters - n_mixed), &done, &r);
+        n_mixed += done;
+        if (rc) return finish(rc);
+        if (r < tol) break;
+        if (r < PROGRESS * best) {
+            stalled = 0;
+        } else if (++stalled >= PATIENCE) {
+            break;
+        }
+        best = std::min(best, r);
+    }
+    if (n_mixed >= max_iters && !(r < tol)) {
+        // the budget ended in the mixed phase
+        if (macros_out && (rc = kgs_moments(m, macros_out))) return finish(rc);
+        return finish(KGS_NOTCONVERGED);
+    }
+    // FP64 phase from the mixed state (same wall densities and mass target)
+    size_t len = 0;
+    if ((rc = kgs_save(m, nullptr, &len))) return finish(rc);
+    state.resize(len);
+    if ((rc = kgs_save(m, state.data(), &len))) return finish(rc);
+    kgs_opts od = opts_for(p, KGS_FP64, tol, std::max(1, max_iters - n_mixed), stream);  // >= 1: confirms tol
+    if ((rc = kgs_setup(&d, &p->grid, p->solid, &p->vgrid, &p->gas, &p->bc, &od))) return finish(rc);
+    if ((rc = kgs_load(d, state.data(), len))) return finish(rc);
+    rc = kgs_iterate(d, 0, &n_fp64, &r);
+    if (rc != KGS_OK && rc != KGS_NOTCONVERGED) return finish(rc);
+    const int status = rc;
+    if (macros_out && (rc = kgs_moments(d, macros_out))) return finish(rc);
+    return finish(status);
+}

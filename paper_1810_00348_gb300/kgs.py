@@ -411,6 +411,28 @@ def kgs_batch_fault(b, spin_limit=20000000, unpublished_item=-1):
     return _check(load().kgs_batch_fault(b.handle, int(spin_limit), int(unpublished_item)), "kgs_batch_fault")
 
 
+SIGNATURES["kgs_solve"] = (ctypes.c_int, [ctypes.POINTER(KgsProblem), _dp, ctypes.c_double, ctypes.c_int, _dp,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp,
+                                          ctypes.c_void_p])
+
+
+def kgs_solve(prob, initial=None, tol=1e-6, max_iters=5000, stream=None):
+    """Mixed iterations while they make progress, then FP64 to tol.  Returns
+    (rc, macros [8, nz, ny, nx], mixed iterations, FP64 iterations,
+    residual); KGS_NOTCONVERGED is returned, other errors raise."""
+    keep = []
+    p = _problem(prob, keep)
+    out = np.empty(8 * prob.ncell)
+    init = None if initial is None else _arr(initial).reshape(-1)
+    nm, nd = ctypes.c_int(0), ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    rc = load().kgs_solve(ctypes.byref(p), init.ctypes.data_as(_dp) if init is not None else _dp(), float(tol),
+                          int(max_iters), out.ctypes.data_as(_dp), ctypes.byref(nm), ctypes.byref(nd),
+                          ctypes.byref(res), ctypes.c_void_p(stream) if stream else None)
+    _check(rc, "kgs_solve", allow=(KGS_NOTCONVERGED,))
+    return rc, out.reshape(8, prob.nz, prob.ny, prob.nx), nm.value, nd.value, res.value
+
+
 def kgs_batch_destroy(b):
     if b.handle:
         load().kgs_batch_destroy(b.handle)
