@@ -313,25 +313,43 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
 #pragma unroll
             for (int q = 0; q < CPF; q++) pc[q] = (q0 + q == C_FLAGS) ? Real(F_SOLID) : Real(0);
         }
+        if (xfirst) {
 #pragma unroll
-        for (int lj2 = 0; lj2 < BY; lj2++) {
-            if (lj2 >= ey) break;
-            const int y = GY(lj2), x = GX(0);
-            const Real rw = xfirst ? wall_rho(sidex, CELL(x, y, z)) : Real(0);
+            for (int lj2 = 0; lj2 < BY; lj2++) {
+                if (lj2 >= ey) break;
+                const Real rw = wall_rho(sidex, CELL(GX(0), GY(lj2), z));
 #pragma unroll
-            for (int m = 0; m < TV; m++)
-                phx[lj2][m] = xfirst ? rw * mgx[m]
-                                     : (ok[m] ? ld_face<COHERENT>(FXp + ((size_t)z * ny + y) * Nv + gv[m]) : Real(0));
+                for (int m = 0; m < TV; m++) phx[lj2][m] = rw * mgx[m];
+            }
+        } else {
+            const Real *fi = FXp + ((size_t)z * ny + GY(0)) * Nv;
+            const long long step = py ? (long long)Nv : -(long long)Nv;
+#pragma unroll
+            for (int lj2 = 0; lj2 < BY; lj2++) {
+                if (lj2 >= ey) break;
+#pragma unroll
+                for (int m = 0; m < TV; m++)
+                    phx[lj2][m] = ok[m] ? ld_face<COHERENT>(fi + lj2 * step + (long long)gv[m]) : Real(0);
+            }
         }
+        if (yfirst) {
 #pragma unroll
-        for (int li2 = 0; li2 < BX; li2++) {
-            if (li2 >= ex) break;
-            const int x = GX(li2), y = GY(0);
-            const Real rw = yfirst ? wall_rho(sidey, CELL(x, y, z)) : Real(0);
+            for (int li2 = 0; li2 < BX; li2++) {
+                if (li2 >= ex) break;
+                const Real rw = wall_rho(sidey, CELL(GX(li2), GY(0), z));
 #pragma unroll
-            for (int m = 0; m < TV; m++)
-                phy[li2][m] = yfirst ? rw * mgy[m]
-                                     : (ok[m] ? ld_face<COHERENT>(FYp + ((size_t)z * nx + x) * Nv + gv[m]) : Real(0));
+                for (int m = 0; m < TV; m++) phy[li2][m] = rw * mgy[m];
+            }
+        } else {
+            const Real *fi = FYp + ((size_t)z * nx + GX(0)) * Nv;
+            const long long step = px ? (long long)Nv : -(long long)Nv;
+#pragma unroll
+            for (int li2 = 0; li2 < BX; li2++) {
+                if (li2 >= ex) break;
+#pragma unroll
+                for (int m = 0; m < TV; m++)
+                    phy[li2][m] = ok[m] ? ld_face<COHERENT>(fi + li2 * step + (long long)gv[m]) : Real(0);
+            }
         }
     };
     prefetch(0);
@@ -403,7 +421,6 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                             if (sol_z) rwz = Real(a.rho_w[sidez * ncell + cell]);
                         }
                         const int sidx = SL(li, lj);
-                        const bool out_x = li == ex - 1 && !xlast, out_y = lj == ey - 1 && !ylast;
 #pragma unroll
                         for (int m = 0; m < TV; m++) {
                             const int vl = t + m * NT;
@@ -424,14 +441,36 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                             const Real num = src + ax * fx + ay * fy + az * fz;
                             const Real den = rtau + ax + ay + az;
                             const Real f = implicit_div(num, den);
-                            if (ok[m]) {
-                                slice[sidx + vl] = f;
-                                if (out_x) FXp[((size_t)z * ny + GY(lj)) * Nv + gv[m]] = f;
-                                if (out_y) FYp[((size_t)z * nx + GX(li)) * Nv + gv[m]] = f;
-                            }
+                            if (ok[m]) slice[sidx + vl] = f;
                         }
                     }
                 }
+            }
+        }
+        // outflow of the slice through the block's downwind x and y faces, for
+        // the neighbouring blocks (own velocities, read back from the slice)
+        if (!xlast) {
+            Real *fo = FXp + ((size_t)z * ny + GY(0)) * Nv;
+            const long long step = py ? (long long)Nv : -(long long)Nv;
+#pragma unroll
+            for (int lj = 0; lj < BY; lj++) {
+                if (lj >= ey) break;
+                const Real *src = slice + SL(ex - 1, lj) + t;
+#pragma unroll
+                for (int m = 0; m < TV; m++)
+                    if (ok[m]) fo[lj * step + (long long)gv[m]] = src[m * NT];
+            }
+        }
+        if (!ylast) {
+            Real *fo = FYp + ((size_t)z * nx + GX(0)) * Nv;
+            const long long step = px ? (long long)Nv : -(long long)Nv;
+#pragma unroll
+            for (int li = 0; li < BX; li++) {
+                if (li >= ex) break;
+                const Real *src = slice + SL(li, ey - 1) + t;
+#pragma unroll
+                for (int m = 0; m < TV; m++)
+                    if (ok[m]) fo[li * step + (long long)gv[m]] = src[m * NT];
             }
         }
         __syncthreads();
