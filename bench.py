@@ -38,9 +38,9 @@ N_CELL, N_VEL, KN, LID = 64, 32, 1.0, 0.16
 # 13 (with the division); 13 moment sums about U^n 34.
 FLOPS_PER_PP = 68
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch (ncu, 32^3
-# cells x 32^3 velocities, 256 velocities per CTA, blocks 8x8x32): 2.143e9 B
+# cells x 32^3 velocities, 256 velocities per CTA, blocks 8x8x32): 2.145e9 B
 # over 1.074e9 phase points
-TRAFFIC_BYTES_PER_PP = 2.143e9 / 1.074e9
+TRAFFIC_BYTES_PER_PP = 2.145e9 / 1.074e9
 TRAFFIC_SHAPE = (256, 32)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -219,7 +219,7 @@ def run_ours(args, world, rank, local):
     # DRAM bytes per launch from an ncu capture of this kernel at 32^3 cells x
     # 32^3 velocities with the same sweep shape, scaled by phase points
     traffic = None
-    if (info["v_per_cta"], info["block_z"]) == TRAFFIC_SHAPE:
+    if TRAFFIC_BYTES_PER_PP and (info["v_per_cta"], info["block_z"]) == TRAFFIC_SHAPE:
         traffic = TRAFFIC_BYTES_PER_PP * pp
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic,
