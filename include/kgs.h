@@ -298,8 +298,11 @@ int kgs_solve(const kgs_problem *prob, const double *initial, double tol, int ma
  * accumulate in FP32 on the tensor cores; the master parameters and Adam
  * moments are FP32.  Channel counts are at most 112.  A network is bound to
  * the device current at creation and works on `stream` (NULL = legacy
- * default stream); calls are ordered on that stream and the functions that
- * return host values synchronise it.  Parameter layout on the host (get/set):
+ * default stream); calls are ordered on that stream and kgs_net_forward,
+ * kgs_net_train_step and the functions that return host values synchronise
+ * it.  The convolutions run on the tensor cores with bounded waits; a wait
+ * that gives up makes kgs_net_forward / kgs_net_train_step return
+ * KGS_ETIMEOUT (no parameter update is made).  Parameter layout on the host (get/set):
  * per layer W[27][Cout][Cin] (tap t = (kz*3 + ky)*3 + kx reads the input at
  * offset (kz-1, ky-1, kx-1)) followed by b[Cout], FP32. */
 typedef struct kgs_net kgs_net;

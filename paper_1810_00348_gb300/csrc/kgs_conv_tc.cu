@@ -1,0 +1,299 @@
+// kgs_conv_tc.cu -- 3x3x3 convolution as an implicit GEMM on the fifth-
+// generation tensor cores (tcgen05.mma, accumulator in tensor memory).
+//
+// GEMM view: out[v][co] = sum over taps t and input channels ci of
+// in[v + off(t)][ci] W[t][co][ci].  A CTA owns 128 output voxels, an 8 (x)
+// by 16 (y) patch of one z-plane, i.e. the M = 128 rows of one MMA, and all
+// output channels (N = cout_p <= 112).  It stages the input halo of the
+// patch (10 x 18 x 3 voxels, all channels) in shared memory once, in the
+// K-major no-swizzle layout the MMA reads: 16-byte rows (8 channels of one
+// voxel), x fastest within a channel octet, so that for every tap the 8 x
+// positions of an output row segment are 8 consecutive 16-byte rows (one
+// 8 x 16 B core matrix) and the 16 y rows and the channel octets are fixed
+// strides.  Each tap is then C/16 MMAs of 128 x N x 16 reading shifted
+// windows of the same halo; no im2col copy is made.  Halo and weights move
+// with asynchronous copies (cp.async); the weights of a tap (N x C) rotate
+// through three buffers: tap t+2 is fetched while the tensor core works on
+// tap t, once a commit barrier shows that tap t-1 has released its buffer.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
+// TMEM lanes 32w..32w+31 = output rows) and applies bias + ReLU, bias only,
+// or the ReLU mask of the backward pass.
+//
+// Every wait on a barrier is bounded; on expiry the CTA records the error,
+// waits (bounded) for its own MMAs, frees its tensor memory and returns.
+#include <cstdint>
+
+#include "kgs_nn.h"
+
+namespace kgs {
+namespace nn {
+namespace {
+
+constexpr int TX = 8, TY = 16;                 // output patch: 128 voxels = 128 GEMM rows
+constexpr int HX = TX + 2, HY = TY + 2, HZ = 3;  // input halo of the patch
+constexpr int THREADS = 128;
+constexpr int TMEM_COLS = 128;                 // >= N, a power of two
+constexpr int NBUF = 3;                        // weight buffers: taps t, t+1, t+2 in flight
+constexpr long long WAIT_POLLS = 1ll << 20;    // try_wait polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major operand without swizzling.
+// lbo: bytes between core matrices adjacent along K; sbo: bytes between core
+// matrices adjacent along M (or N).  Bits 46-47 hold the descriptor version
+// (1 on this architecture family); base offset, LBO mode and layout type 0.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), bf16
+// A and B (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 in
+// bits 17-22, M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (long long i = 0; i < WAIT_POLLS; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 16-byte asynchronous global -> shared copy; zero-fills when !valid (no
+// global read is made then; src must still be a valid address).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+    conv_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ w,
+                   const float *__restrict__ bias, void *out, const __nv_bfloat16 *__restrict__ gate, ConvDims dm,
+                   int *err)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar[NBUF];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail, s_last;  // a wait gave up; last tap whose MMAs were committed
+
+    const int C8 = dm.cin_p / 8, cout_p = dm.cout_p;
+    const size_t halo_bytes = (size_t)HZ * HY * C8 * HX * 16;
+    const size_t w_bytes = (size_t)C8 * cout_p * 16;
+    unsigned char *halo = sm;
+    unsigned char *wbuf = sm + halo_bytes;
+    const int tiles_x = (dm.W + TX - 1) / TX;
+    const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+    const int z = blockIdx.y, b = blockIdx.z;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    auto bar = [&](int t) { return smem_u32(&mbar[t % NBUF]); };  // commit barrier of tap t
+    auto parity = [](int t) { return (uint32_t)((t / NBUF) & 1); };
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NBUF; q++) mbar_init(smem_u32(&mbar[q]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+        s_last = -1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+
+    // input halo: element (hx, hy, hz, channel octet c8) at ((hz*HY + hy)*C8 + c8)*HX + hx
+    const size_t vol = (size_t)dm.D * dm.H * dm.W;
+    const uint32_t halo_a = smem_u32(halo), w_a = smem_u32(wbuf);
+    for (int i = threadIdx.x; i < HZ * HY * HX * C8; i += THREADS) {
+        const int c8 = i % C8, r = i / C8;
+        const int hx = r % HX, hy = (r / HX) % HY, hz = r / (HX * HY);
+        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z - 1 + hz;
+        const bool valid = gx >= 0 && gy >= 0 && gz >= 0 && gx < dm.W && gy < dm.H && gz < dm.D;
+        const __nv_bfloat16 *src =
+            valid ? in + ((size_t)b * vol + ((size_t)gz * dm.H + gy) * dm.W + gx) * dm.cin_p + c8 * 8 : in;
+        cp_async16(halo_a + (uint32_t)(((hz * HY + hy) * C8 + c8) * HX + hx) * 16, src, valid);
+    }
+    cp_async_commit();
+    // weights of tap t into buffer t % NBUF: element (co, octet c8) at c8*cout_p + co
+    auto load_w = [&](int t) {
+        const __nv_bfloat16 *src = w + (size_t)t * cout_p * dm.cin_p;
+        const uint32_t dst = w_a + (uint32_t)((t % NBUF) * w_bytes);
+        for (int i = threadIdx.x; i < cout_p * C8; i += THREADS) {
+            const int c8 = i % C8, co = i / C8;
+            cp_async16(dst + (uint32_t)(c8 * cout_p + co) * 16, src + (size_t)co * dm.cin_p + c8 * 8, true);
+        }
+        cp_async_commit();
+    };
+    load_w(0);
+    load_w(1);
+    const uint32_t idesc = instr_desc(128, cout_p);
+    const uint32_t a_lbo = HX * 16, a_sbo = (uint32_t)C8 * HX * 16;
+    const uint32_t b_lbo = (uint32_t)cout_p * 16, b_sbo = 8 * 16;
+
+    for (int t = 0; t < 27; t++) {
+        // the copies of the halo and of tap t have landed (tap t+1 may be in flight)
+        if (t < 26)
+            cp_async_wait<1>();
+        else
+            cp_async_wait<0>();
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
+        if (threadIdx.x == 0 && !s_fail) {
+            const uint32_t tmem = tmem_base;
+            for (int kc = 0; kc < C8 / 2; kc++) {
+                const uint64_t a = smem_desc(halo_a + (uint32_t)((((kz * HY + ky) * C8 + 2 * kc) * HX + kx) * 16),
+                                             a_lbo, a_sbo);
+                const uint64_t bd =
+                    smem_desc(w_a + (uint32_t)((t % NBUF) * w_bytes + (size_t)2 * kc * cout_p * 16), b_lbo, b_sbo);
+                tc_mma(tmem, a, bd, idesc, (t | kc) != 0);
+            }
+            tc_commit(bar(t));
+            s_last = t;
+        }
+        if (t + 2 < 27) {
+            // buffer (t+2) % NBUF was read by tap t-1: wait for its commit
+            if (t >= 1 && !s_fail && !mbar_wait(bar(t - 1), parity(t - 1))) s_fail = 1;
+            load_w(t + 2);
+        }
+    }
+    // all MMAs of the CTA are complete once the last commit has arrived (on
+    // failure: the last commit that was made, so that no MMA still writes the
+    // tensor memory freed below)
+    __syncthreads();
+    const uint32_t tmem = tmem_base;
+    const int last = s_last;
+    const bool done = last >= 0 && mbar_wait(bar(last), parity(last));
+    tc_fence_after();
+    if (!done || s_fail || last != 26) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else {
+        const int row = warp * 32 + lane;
+        const int vx = x0 + row % TX, vy = y0 + row / TX;
+        const bool inside = vx < dm.W && vy < dm.H;
+        const size_t vo = (size_t)b * vol + ((size_t)z * dm.H + vy) * dm.W + vx;
+        for (int c0 = 0; c0 < cout_p; c0 += 16) {
+            float v[16];
+            tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);  // all lanes take part
+            if (!inside) continue;
+            if (MODE == 1) {
+                float *o = static_cast<float *>(out) + vo * cout_p + c0;
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4 *>(o + i) =
+                        make_float4(v[i] + bias[c0 + i], v[i + 1] + bias[c0 + i + 1], v[i + 2] + bias[c0 + i + 2],
+                                    v[i + 3] + bias[c0 + i + 3]);
+            } else {
+                __align__(16) __nv_bfloat162 h[8];
+                if (MODE == 0) {
+#pragma unroll
+                    for (int i = 0; i < 8; i++)
+                        h[i] = __floats2bfloat162_rn(fmaxf(v[2 * i] + bias[c0 + 2 * i], 0.f),
+                                                     fmaxf(v[2 * i + 1] + bias[c0 + 2 * i + 1], 0.f));
+                } else {
+                    __align__(16) __nv_bfloat162 g[8];
+                    const uint4 *gp = reinterpret_cast<const uint4 *>(gate + vo * cout_p + c0);
+                    reinterpret_cast<uint4 *>(g)[0] = gp[0];
+                    reinterpret_cast<uint4 *>(g)[1] = gp[1];
+#pragma unroll
+                    for (int i = 0; i < 8; i++)
+                        h[i] = __floats2bfloat162_rn(__bfloat162float(g[i].x) > 0.f ? v[2 * i] : 0.f,
+                                                     __bfloat162float(g[i].y) > 0.f ? v[2 * i + 1] : 0.f);
+                }
+                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + vo * cout_p + c0);
+                o[0] = reinterpret_cast<uint4 *>(h)[0];
+                o[1] = reinterpret_cast<uint4 *>(h)[1];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+template <int MODE>
+cudaError_t launch(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
+                   const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
+{
+    const size_t smem = (size_t)HZ * HY * (dm.cin_p / 8) * HX * 16 + NBUF * (size_t)(dm.cin_p / 8) * dm.cout_p * 16;
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((dm.W + TX - 1) / TX) * ((dm.H + TY - 1) / TY);
+    conv_tc_kernel<MODE><<<dim3(tiles, dm.D, dm.B), THREADS, smem, s>>>(in, w, bias, out, gate, dm, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t conv_tc(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
+                    const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
+{
+    if (dm.cin_p % 16 || dm.cout_p % 16 || dm.cin_p < 16 || dm.cout_p < 16 || dm.cin_p > 112 || dm.cout_p > 112)
+        return cudaErrorInvalidValue;
+    switch (mode) {
+    case 0: return launch<0>(in, w, bias, out, gate, dm, err, s);
+    case 1: return launch<1>(in, w, bias, out, gate, dm, err, s);
+    default: return launch<2>(in, w, bias, out, gate, dm, err, s);
+    }
+}
+
+}  // namespace nn
+}  // namespace kgs

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "../../include/kgs.h"
+#include "kgs_nn.h"
 
 namespace {
 
@@ -69,133 +70,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-struct ConvDims {
-    int B, D, H, W;  // batch and volume
-    int cin_p, cout_p;
-};
-
-// ---------------------------------------------------------------------------
-// Forward (and data-gradient) convolution.
-//   in   [B][D][H][W][cin_p]   bf16
-//   w    [27][cout_p][cin_p]   bf16 (per tap: output-channel rows, input channels contiguous)
-//   bias [cout_p] FP32 or NULL
-//   MODE 0: out = relu(acc + bias) -> bf16
-//   MODE 1: out = acc + bias -> FP32 (last layer)
-//   MODE 2: out = acc * (gate > 0) -> bf16 (ReLU derivative of the layer below,
-//           gate = that layer's stored activation, same layout as out)
-// CTA: one 4x4x4 voxel tile of one sample, all output channels.  Warp w owns
-// voxels 16w..16w+15 of the tile; per k-step of 16 input channels it issues
-// cout_p/8 mma over the tap's shifted voxels.
-template <int MODE>
-__global__ void __launch_bounds__(CONV_THREADS) conv_fwd_kernel(const __nv_bfloat16 *__restrict__ in,
-                                                                const __nv_bfloat16 *__restrict__ w,
-                                                                const float *__restrict__ bias, void *out,
-                                                                const __nv_bfloat16 *__restrict__ gate, ConvDims dm)
-{
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int cin_p = dm.cin_p, cout_p = dm.cout_p;
-    const int hs = cin_p + 8;   // halo row stride (bf16): +16 bytes against bank conflicts
-    const int ws = cin_p + 8;   // weight row stride
-    __nv_bfloat16 *halo = reinterpret_cast<__nv_bfloat16 *>(sm);             // [HV][hs]
-    __nv_bfloat16 *wt = halo + HV * hs;                                      // [2][cout_p][ws]
-    const int tiles_x = (dm.W + TILE - 1) / TILE, tiles_y = (dm.H + TILE - 1) / TILE;
-    const int tx = blockIdx.x % tiles_x, ty = (blockIdx.x / tiles_x) % tiles_y, tz = blockIdx.x / (tiles_x * tiles_y);
-    const int b = blockIdx.y;
-    const int x0 = tx * TILE - 1, y0 = ty * TILE - 1, z0 = tz * TILE - 1;
-    const size_t vol = (size_t)dm.D * dm.H * dm.W;
-    const __nv_bfloat16 *inb = in + (size_t)b * vol * cin_p;
-
-    // halo tile (zero outside the volume), 16-byte chunks
-    const int cch = cin_p / 8;
-    for (int i = threadIdx.x; i < HV * cch; i += CONV_THREADS) {
-        const int hv = i / cch, ch = i % cch;
-        const int hx = hv % HALO, hy = (hv / HALO) % HALO, hz = hv / (HALO * HALO);
-        const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (gx >= 0 && gy >= 0 && gz >= 0 && gx < dm.W && gy < dm.H && gz < dm.D)
-            val = *reinterpret_cast<const uint4 *>(inb + (((size_t)gz * dm.H + gy) * dm.W + gx) * cin_p + ch * 8);
-        *reinterpret_cast<uint4 *>(halo + hv * hs + ch * 8) = val;
-    }
-    auto load_w = [&](int t, int buf) {
-        const __nv_bfloat16 *src = w + (size_t)t * cout_p * cin_p;
-        __nv_bfloat16 *dst = wt + (size_t)buf * cout_p * ws;
-        for (int i = threadIdx.x; i < cout_p * cch; i += CONV_THREADS) {
-            const int r = i / cch, ch = i % cch;
-            *reinterpret_cast<uint4 *>(dst + r * ws + ch * 8) =
-                *reinterpret_cast<const uint4 *>(src + (size_t)r * cin_p + ch * 8);
-        }
-    };
-    load_w(0, 0);
-    __syncthreads();
-
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int ntile = cout_p / 8;  // n8 tiles
-    float acc[14][4];              // cout_p <= 112
-#pragma unroll
-    for (int j = 0; j < 14; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    // this lane's A row (ldmatrix x4: rows 0-15 of the warp's block, k halves)
-    const int arow = (lane & 7) + ((lane >> 3) & 1) * 8;
-    const int akof = (lane >> 4) * 8;
-    const int m = warp * 16 + arow;  // voxel of the tile
-    const int lx = m % TILE, ly = (m / TILE) % TILE, lz = m / (TILE * TILE);
-    // B rows (ldmatrix x4 over two n8 tiles): n = (lane & 7) + (lane >> 4) * 8, k half by bit 3
-    const int brow = (lane & 7) + (lane >> 4) * 8;
-    const int bkof = ((lane >> 3) & 1) * 8;
-
-    for (int t = 0; t < 27; t++) {
-        const int buf = t & 1;
-        if (t + 1 < 27) load_w(t + 1, buf ^ 1);
-        const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
-        const int hv = ((lz + kz) * HALO + (ly + ky)) * HALO + (lx + kx);
-        const __nv_bfloat16 *arowp = halo + hv * hs + akof;
-        const __nv_bfloat16 *wb = wt + (size_t)buf * cout_p * ws;
-        for (int kc = 0; kc < cin_p; kc += 16) {
-            unsigned a0, a1, a2, a3;
-            ldsm_x4(smem_addr(arowp + kc), a0, a1, a2, a3);
-#pragma unroll
-            for (int j2 = 0; j2 < 7; j2++) {
-                if (2 * j2 >= ntile) break;
-                unsigned b0, b1, b2, b3;
-                ldsm_x4(smem_addr(wb + (j2 * 16 + brow) * ws + kc + bkof), b0, b1, b2, b3);
-                mma_bf16(acc[2 * j2], a0, a1, a2, a3, b0, b1);
-                if (2 * j2 + 1 < ntile) mma_bf16(acc[2 * j2 + 1], a0, a1, a2, a3, b2, b3);
-            }
-        }
-        __syncthreads();  // next tap's weights loaded, this tap's done
-    }
-
-    // epilogue: rows g and g+8 of the warp's 16 voxels, columns 2*(lane%4)+{0,1}
-    const int g = lane >> 2, cpair = (lane & 3) * 2;
-#pragma unroll
-    for (int half = 0; half < 2; half++) {
-        const int mm = warp * 16 + g + half * 8;
-        const int vx = tx * TILE + mm % TILE, vy = ty * TILE + (mm / TILE) % TILE, vz = tz * TILE + mm / (TILE * TILE);
-        if (vx >= dm.W || vy >= dm.H || vz >= dm.D) continue;
-        const size_t vo = (size_t)b * vol + ((size_t)vz * dm.H + vy) * dm.W + vx;
-#pragma unroll
-        for (int j = 0; j < 14; j++) {
-            if (j >= ntile) break;
-            const int co = j * 8 + cpair;
-            float v0 = acc[j][half * 2], v1 = acc[j][half * 2 + 1];
-            if (MODE != 2 && bias) {
-                v0 += bias[co];
-                v1 += bias[co + 1];
-            }
-            if (MODE == 0) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
-                reinterpret_cast<__nv_bfloat162 *>(out)[(vo * cout_p + co) / 2] = __floats2bfloat162_rn(v0, v1);
-            } else if (MODE == 1) {
-                reinterpret_cast<float2 *>(out)[(vo * cout_p + co) / 2] = make_float2(v0, v1);
-            } else {
-                const __nv_bfloat162 gt = reinterpret_cast<const __nv_bfloat162 *>(gate)[(vo * cout_p + co) / 2];
-                v0 = __bfloat162float(gt.x) > 0.f ? v0 : 0.f;
-                v1 = __bfloat162float(gt.y) > 0.f ? v1 : 0.f;
-                reinterpret_cast<__nv_bfloat162 *>(out)[(vo * cout_p + co) / 2] = __floats2bfloat162_rn(v0, v1);
-            }
-        }
-    }
-}
+using kgs::nn::ConvDims;
 
 // ---------------------------------------------------------------------------
 // Weight gradient: part[chunk][t][co][ci] = sum over the chunk's voxels v of
@@ -490,23 +365,12 @@ __global__ void apply_kernel(size_t ncell, const double *__restrict__ up, const 
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-size_t conv_fwd_smem(int cin_p, int cout_p)
-{
-    return (size_t)HV * (cin_p + 8) * 2 + 2 * (size_t)cout_p * (cin_p + 8) * 2;
-}
-
 size_t wgrad_smem(int cin_p, int cout_p) { return (size_t)HV * (cin_p + 8) * 2 + (size_t)TV_ * (cout_p + 8) * 2; }
 
-template <int MODE>
-cudaError_t run_conv(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
-                     const __nv_bfloat16 *gate, ConvDims dm, cudaStream_t s)
+cudaError_t run_conv(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
+                     const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
 {
-    const size_t smem = conv_fwd_smem(dm.cin_p, dm.cout_p);
-    cudaError_t e = cudaFuncSetAttribute(conv_fwd_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int tiles = ((dm.W + TILE - 1) / TILE) * ((dm.H + TILE - 1) / TILE) * ((dm.D + TILE - 1) / TILE);
-    conv_fwd_kernel<MODE><<<dim3(tiles, dm.B), CONV_THREADS, smem, s>>>(in, w, bias, out, gate, dm);
-    return cudaGetLastError();
+    return kgs::nn::conv_tc(mode, in, w, bias, out, gate, dm, err, s);
 }
 
 }  // namespace
@@ -535,6 +399,8 @@ struct kgs_net {
     float *loss_part = nullptr;
     size_t loss_part_cap = 0;
     float *h_loss = nullptr;
+    int *d_err = nullptr;  // set by a convolution whose bounded wait gave up
+    int *h_err = nullptr;  // pinned copy
 };
 
 namespace {
@@ -583,6 +449,20 @@ int ensure_shape(kgs_net *n, int B, int D, int H, int W)
     return KGS_OK;
 }
 
+// Synchronise the network's stream and report a convolution whose bounded
+// wait gave up (KGS_ETIMEOUT; the word is cleared for the next call).
+int sync_and_check(kgs_net *n)
+{
+    NN_CHECK(cudaMemcpyAsync(n->h_err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream));
+    NN_CHECK(cudaStreamSynchronize(n->stream));
+    if (*n->h_err) {
+        *n->h_err = 0;
+        NN_CHECK(cudaMemset(n->d_err, 0, sizeof(int)));
+        return KGS_ETIMEOUT;
+    }
+    return KGS_OK;
+}
+
 ConvDims dims(const kgs_net *n, int l) { return ConvDims{n->B, n->D, n->H, n->W, n->cp[l], n->cp[l + 1]}; }
 
 int forward(kgs_net *n, const float *x)
@@ -595,9 +475,9 @@ int forward(kgs_net *n, const float *x)
         const __nv_bfloat16 *w = n->pb + n->w_off[l];
         const float *bias = n->p + n->b_off[l];
         if (l < n->L - 1)
-            NN_CHECK(run_conv<0>(n->act[l], w, bias, n->act[l + 1], nullptr, dims(n, l), s));
+            NN_CHECK(run_conv(0, n->act[l], w, bias, n->act[l + 1], nullptr, dims(n, l), n->d_err, s));
         else
-            NN_CHECK(run_conv<1>(n->act[l], w, bias, n->out, nullptr, dims(n, l), s));
+            NN_CHECK(run_conv(1, n->act[l], w, bias, n->out, nullptr, dims(n, l), n->d_err, s));
     }
     return KGS_OK;
 }
@@ -635,7 +515,7 @@ int backward(kgs_net *n)
         transpose_w_kernel<<<nblk(per, 256), 256, 0, s>>>(n->pb + n->w_off[l], dm.cout_p, dm.cin_p, n->wt);
         NN_CHECK(cudaGetLastError());
         const ConvDims db{n->B, n->D, n->H, n->W, dm.cout_p, dm.cin_p};
-        NN_CHECK(run_conv<2>(gcur, n->wt, nullptr, gnext, n->act[l], db, s));
+        NN_CHECK(run_conv(2, gcur, n->wt, nullptr, gnext, n->act[l], db, n->d_err, s));
         std::swap(gcur, gnext);
     }
     return KGS_OK;
@@ -698,8 +578,10 @@ int kgs_net_create(kgs_net **out, int n_layers, const int *channels, unsigned lo
     if (cudaMalloc(&n->p, off * 4) != cudaSuccess || cudaMalloc(&n->g, off * 4) != cudaSuccess ||
         cudaMalloc(&n->m1, off * 4) != cudaSuccess || cudaMalloc(&n->m2, off * 4) != cudaSuccess ||
         cudaMalloc(&n->pb, off * 2) != cudaSuccess || cudaMalloc(&n->wt, wmax * 2) != cudaSuccess ||
-        cudaMallocHost(&n->h_loss, sizeof(float)) != cudaSuccess)
+        cudaMallocHost(&n->h_loss, sizeof(float)) != cudaSuccess || cudaMalloc(&n->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&n->h_err, sizeof(int)) != cudaSuccess)
         return fail(KGS_ENOMEM);
+    if (cudaMemset(n->d_err, 0, sizeof(int)) != cudaSuccess) return fail(KGS_ECUDA);
     if (cudaMemcpy(n->p, h.data(), off * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(n->g, 0, off * 4) != cudaSuccess || cudaMemset(n->m1, 0, off * 4) != cudaSuccess ||
         cudaMemset(n->m2, 0, off * 4) != cudaSuccess)
@@ -780,7 +662,7 @@ int kgs_net_forward(kgs_net *n, const float *x, int B, int D, int H, int W, floa
     unpack_output_kernel<<<nblk(nvox * n->c[n->L], 256), 256, 0, n->stream>>>(n->out, nvox, n->cp[n->L],
                                                                               n->c[n->L], y);
     NN_CHECK(cudaGetLastError());
-    return KGS_OK;
+    return sync_and_check(n);
 }
 
 int kgs_net_train_step(kgs_net *n, const float *x, const float *target, const uint8_t *mask, int B, int D, int H,
@@ -814,7 +696,7 @@ int kgs_net_train_step(kgs_net *n, const float *x, const float *target, const ui
     mse_kernel<<<nb, 256, 0, n->stream>>>(n->out, target, mask, nvox, cpL, cL, 1.f / (count * cL), n->ga,
                                           n->loss_part);
     NN_CHECK(cudaGetLastError());
-    if ((rc = backward(n))) return rc;
+    if ((rc = backward(n)) || (rc = sync_and_check(n))) return rc;  // no update from an incomplete pass
     n->step++;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
@@ -883,6 +765,8 @@ void kgs_net_destroy(kgs_net *n)
     if (n->pb) cudaFree(n->pb);
     if (n->wt) cudaFree(n->wt);
     if (n->h_loss) cudaFreeHost(n->h_loss);
+    if (n->d_err) cudaFree(n->d_err);
+    if (n->h_err) cudaFreeHost(n->h_err);
     delete n;
 }
 
