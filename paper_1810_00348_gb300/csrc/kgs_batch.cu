@@ -26,7 +26,7 @@ struct kgs_batch {
     bool own_stream = false;  // graphs cannot be captured on the legacy default stream
     int n = 0;
     std::vector<kgs_ctx *> ctx;
-    int precision = KGS_MIXED, tv = 2, bz = 32, line16 = 0, nxo_max = 1;
+    int precision = KGS_MIXED, tv = 2, bz = 32, line16 = 0, uniform = 0, nxo_max = 1;
     int max_iters = 1000;
     double tol = 1e-8;
     std::vector<char> active;
@@ -127,7 +127,7 @@ int enqueue_iteration(kgs_batch *b, int which)
     ba.skip_publish = b->skip_publish;
     // external records: inside a capture a plain record only orders streams
     KGS_CHECK(cudaEventRecordWithFlags(b->ev[0], st, cudaEventRecordExternal));
-    KGS_CHECK(launch_sweep_persistent(b->precision, b->tv, b->line16, ba, b->nxo_max, b->grid, st));
+    KGS_CHECK(launch_sweep_persistent(b->precision, b->tv, b->line16, b->uniform, ba, b->nxo_max, b->grid, st));
     KGS_CHECK(cudaEventRecordWithFlags(b->ev[1], st, cudaEventRecordExternal));
     for (int i = 0; i < b->n; i++)
         if (b->active[i] && (rc = ctx_launch_closure(b->ctx[i], b->d_resid + 2 * i))) return rc;
@@ -231,6 +231,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     b->done.assign(n, 0);
     std::vector<int> flag_off(n);
     b->line16 = 1;
+    b->uniform = 1;
     for (int i = 0; i < n; i++) {
         const kgs_problem &p = probs[i];
         kgs_opts o = *opts;
@@ -247,6 +248,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
         b->nxo_max = std::max(b->nxo_max, t.nxo_max);
         for (int q = 0; q < 8; q++)
             if (t.oct_vcount[q] > 0 && t.oct_nx[q] != 16) b->line16 = 0;
+        if (!ctx_sweep_args(b->ctx[i]).uniform) b->uniform = 0;
         flag_off[i] = (int)b->n_flags;
         b->n_flags += (size_t)t.n_vg * t.nbx * t.nby * t.nbz;
     }
@@ -270,7 +272,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess) return fail(KGS_ECUDA);
     const size_t smem = sweep_smem_bytes(b->precision, b->tv, b->nxo_max);
-    per_sm = sweep_persistent_occupancy(b->precision, b->tv, b->line16, smem);
+    per_sm = sweep_persistent_occupancy(b->precision, b->tv, b->line16, b->uniform, smem);
     if (per_sm < 1) return fail(KGS_ECUDA);
     b->grid = sms * per_sm;
     *out = b;

@@ -46,7 +46,8 @@ __global__ void coef_kernel(const double *__restrict__ mac, const uint8_t *__res
         out[C_UX] = (Real)mac[1 * ncell + c];
         out[C_UY] = (Real)mac[2 * ncell + c];
         out[C_UZ] = (Real)mac[3 * ncell + c];
-        out[C_KAPPA] = (Real)(rtau * A);
+        // the FP32 sweep takes kappa as log2(kappa) inside its exponent
+        out[C_KAPPA] = sizeof(Real) == 8 ? (Real)(rtau * A) : (Real)log2(rtau * A);
         out[C_NEXP] = sizeof(Real) == 8 ? (Real)(-1.0 / (2.0 * RT)) : (Real)(-LOG2E / (2.0 * RT));
         out[C_RT1] = (Real)(1.0 / RT);
         out[C_QX] = (Real)(sh * mac[5 * ncell + c]);
@@ -57,7 +58,7 @@ __global__ void coef_kernel(const double *__restrict__ mac, const uint8_t *__res
         out[C_RDY] = (Real)rdy[j];
         out[C_RDZ] = (Real)rdz[k];
     }
-    out[C_FLAGS] = (Real)flags;
+    out[C_FLAGS] = flag_value<Real>(flags);
     for (int q = 0; q < NCOEF; q++) coef[c * NCOEF + q] = out[q];
 }
 

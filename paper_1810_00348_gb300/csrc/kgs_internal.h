@@ -22,11 +22,11 @@ constexpr int NPART = 16;        // per-cell partial: 13 moment sums + 3 wall fl
 // iteration, stored in the sweep precision).
 enum {
     C_UX = 0, C_UY, C_UZ,   // lagged velocity U^n: centre of c = xi - U^n
-    C_KAPPA,                // (1/tau) rho (2 pi R T)^{-3/2}
+    C_KAPPA,                // (1/tau) rho (2 pi R T)^{-3/2}; FP32 path: its base-2 logarithm
     C_NEXP,                 // exponent scale: -1/(2RT) (FP64) or -log2(e)/(2RT) (FP32)
     C_RT1,                  // 1/(R T)
     C_RTAU,                 // 1/tau
-    C_FLAGS,                // cell flags (below), stored as a small integer value
+    C_FLAGS,                // cell flags (below), their bits stored in the value (flag_value)
     C_QX, C_QY, C_QZ,       // (1 - Pr) q / (5 p R T)
     C_RDX, C_RDY, C_RDZ,    // 1/dx_i, 1/dy_j, 1/dz_k
     C_PAD0, C_PAD1
@@ -74,6 +74,8 @@ struct SweepArgs {
                                   // with value s - c (FP32 path, Kahan pair)
     unsigned long long ncell;
     int line16;                   // every octant has x-lines of 16 nodes (specialised moment loop)
+    int uniform;                  // equal cell widths along each axis: a_d is per velocity
+    double rd0[3];                // 1/dx, 1/dy, 1/dz of a uniform grid
 };
 
 // Persistent sweep over the work items of many instances (one launch per
@@ -92,10 +94,45 @@ struct BatchSweepArgs {
     int skip_publish;             // fault injection: this item never sets its flag (-1: none)
 };
 
-cudaError_t launch_sweep_persistent(int precision, int tv, int line16, const BatchSweepArgs &b, int nxo_max,
+// Cell flags travel in the coefficient array as the bit pattern of a Real
+// (no conversion instruction on either side).
+__host__ __device__ inline float flag_value_f(int f)
+{
+    union {
+        int i;
+        float v;
+    } u;
+    u.i = f;
+    return u.v;
+}
+__host__ __device__ inline double flag_value_d(int f)
+{
+    union {
+        long long i;
+        double v;
+    } u;
+    u.i = f;
+    return u.v;
+}
+template <typename Real>
+__host__ __device__ inline Real flag_value(int f);
+template <>
+__host__ __device__ inline float flag_value<float>(int f)
+{
+    return flag_value_f(f);
+}
+template <>
+__host__ __device__ inline double flag_value<double>(int f)
+{
+    return flag_value_d(f);
+}
+__device__ __forceinline__ int flag_bits(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int flag_bits(double v) { return (int)__double_as_longlong(v); }
+
+cudaError_t launch_sweep_persistent(int precision, int tv, int line16, int uniform, const BatchSweepArgs &b, int nxo_max,
                                     int grid, cudaStream_t s);
 // Resident CTAs per SM of the persistent kernel (also sets its shared-memory limit).
-int sweep_persistent_occupancy(int precision, int tv, int line16, size_t smem);
+int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem);
 
 // Sweep launch (one wavefront stage).  precision: 0 FP64, 1 FP32.
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s);

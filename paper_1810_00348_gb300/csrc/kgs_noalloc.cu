@@ -175,6 +175,7 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
         if (t.oct_vcount[o] > 0 && t.oct_nx[o] != 16) a.line16 = 0;
     }
     a.any_solid = t.any_solid ? 1 : 0;
+    t.set_uniformity(a);
     a.coef = coef;
     a.rho_w = rho_w_in;
     a.mtab = b + o_mt;

@@ -169,6 +169,7 @@ SweepArgs kgs::ctx_sweep_args(const kgs_ctx *c)
     a.line16 = 1;
     for (int o = 0; o < 8; o++)
         if (t.oct_vcount[o] > 0 && t.oct_nx[o] != 16) a.line16 = 0;
+    t.set_uniformity(a);
     return a;
 }
 
@@ -204,7 +205,8 @@ int kgs::ctx_launch_stages(kgs_ctx *c)
         ba.spin_limit = c->spin_limit;
         ba.skip_publish = -1;
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[0], st));
-        KGS_CHECK(launch_sweep_persistent(t.precision, t.tv, a.line16, ba, t.nxo_max, c->persist_grid, st));
+        KGS_CHECK(
+            launch_sweep_persistent(t.precision, t.tv, a.line16, a.uniform, ba, t.nxo_max, c->persist_grid, st));
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[1], st));
         c->kernel_launches += 1;
         c->sweep_launches += 1;
@@ -241,9 +243,9 @@ int kgs::ctx_persist_init(kgs_ctx *c)
     const HostTables &t = c->t;
     int sms = 0;
     KGS_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
-    const int line16 = ctx_sweep_args(c).line16;
-    const int per_sm =
-        sweep_persistent_occupancy(t.precision, t.tv, line16, sweep_smem_bytes(t.precision, t.tv, t.nxo_max));
+    const SweepArgs a = ctx_sweep_args(c);
+    const int per_sm = sweep_persistent_occupancy(t.precision, t.tv, a.line16, a.uniform,
+                                                  sweep_smem_bytes(t.precision, t.tv, t.nxo_max));
     if (per_sm < 1) return KGS_OK;  // keep the launch per stage
     std::vector<int4> items;
     for (int s = 0; s < (int)t.stage_n.size(); s++) ctx_stage_items(t, 0, s, items);

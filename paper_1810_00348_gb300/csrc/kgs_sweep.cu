@@ -181,7 +181,7 @@ __device__ __forceinline__ Real ld_face(const Real *p)
 
 // One work item: block w = (octant, reflected block coordinates) and
 // velocity group vgy of that octant.  Called by every thread of the CTA.
-template <typename Real, int TV, int LINE, bool COHERENT>
+template <typename Real, int TV, int LINE, bool COHERENT, bool UNIF>
 __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, const int vgy, unsigned char *smem)
 {
     using L = SmemLayout<Real, TV>;
@@ -271,6 +271,20 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         mgz[m] = mt[(size_t)rowz * Nv + gv[m]];
         msol[m] = mt[(size_t)MT_SOLID * Nv + gv[m]];
     }
+    // uniform grid: the upwind coefficients a_d = abs(xi_d) / dx_d and their
+    // sum depend on the velocity only
+    Real adx[TV][3], asum[TV];
+#pragma unroll
+    for (int m = 0; m < TV; m++) {
+        if constexpr (UNIF) {
+            adx[m][0] = axi[m][0] * Real(a.rd0[0]);
+            adx[m][1] = axi[m][1] * Real(a.rd0[1]);
+            adx[m][2] = axi[m][2] * Real(a.rd0[2]);
+            asum[m] = adx[m][0] + adx[m][1] + adx[m][2];
+        } else {
+            adx[m][0] = adx[m][1] = adx[m][2] = asum[m] = Real(0);
+        }
+    }
     // x nodes of the octant in line order (the first nxo velocities of the octant)
     for (int ix = t; ix < nxo; ix += NT) {
         const size_t g = (size_t)a.oct_vstart[o] + ix;
@@ -311,7 +325,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
             for (int q = 0; q < CPF; q++) pc[q] = src[q];
         } else {
 #pragma unroll
-            for (int q = 0; q < CPF; q++) pc[q] = (q0 + q == C_FLAGS) ? Real(F_SOLID) : Real(0);
+            for (int q = 0; q < CPF; q++) pc[q] = (q0 + q == C_FLAGS) ? flag_value<Real>(F_SOLID) : Real(0);
         }
         if (xfirst) {
 #pragma unroll
@@ -405,7 +419,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                                      c3 = load_quad(c + 12);
                     const Real ux = c0.x, uy = c0.y, uz = c0.z, kappa = c0.w;
                     const Real nexp = c1.x, rt1 = c1.y, rtau = c1.z;
-                    const int flags = (int)c1.w;
+                    const int flags = flag_bits(c1.w);
                     const Real qx = c2v.x, qy = c2v.y, qz = c2v.z, rdx = c2v.w;
                     const Real rdy = c3.x, rdz = c3.y;
                     if (!(flags & F_SOLID)) {
@@ -435,11 +449,24 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                             const Real cx = xi[m][0] - ux, cy = xi[m][1] - uy, cz = xi[m][2] - uz;
                             const Real c2 = cx * cx + cy * cy + cz * cz;
                             const Real cq = cx * qx + cy * qy + cz * qz;
-                            const Real E = eq_exp(c2 * nexp);
-                            const Real src = kappa * E * (Real(1) + cq * (c2 * rt1 - Real(5)));
-                            const Real ax = axi[m][0] * rdx, ay = axi[m][1] * rdy, az = axi[m][2] * rdz;
+                            Real src;
+                            if constexpr (sizeof(Real) == 4)  // kappa enters as log2(kappa) in the exponent
+                                src = eq_exp(fma(c2, nexp, kappa)) * (Real(1) + cq * (c2 * rt1 - Real(5)));
+                            else
+                                src = kappa * eq_exp(c2 * nexp) * (Real(1) + cq * (c2 * rt1 - Real(5)));
+                            Real ax, ay, az, den;
+                            if constexpr (UNIF) {
+                                ax = adx[m][0];
+                                ay = adx[m][1];
+                                az = adx[m][2];
+                                den = rtau + asum[m];
+                            } else {
+                                ax = axi[m][0] * rdx;
+                                ay = axi[m][1] * rdy;
+                                az = axi[m][2] * rdz;
+                                den = rtau + ax + ay + az;
+                            }
                             const Real num = src + ax * fx + ay * fy + az * fz;
-                            const Real den = rtau + ax + ay + az;
                             const Real f = implicit_div(num, den);
                             if (ok[m]) slice[sidx + vl] = f;
                         }
@@ -481,7 +508,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
             const int li = cl % BX, lj = cl / BX;
             const bool valid = li < ex && lj < ey;
             const Real *c = cs + cl * NCOEF;
-            const int flags = (int)c[C_FLAGS + 0];
+            const int flags = flag_bits(c[C_FLAGS + 0]);
             RunSum<Real> S[NPART];
             if (valid && !(flags & F_SOLID)) {
                 const Real ux = c[C_UX], uy = c[C_UY], uz = c[C_UZ];
@@ -629,11 +656,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
 }
 
 // One wavefront stage: CTA (x, y) = (work item x of the stage, velocity group y).
-template <typename Real, int TV, int LINE>
+template <typename Real, int TV, int LINE, bool UNIF>
 __global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    sweep_item<Real, TV, LINE, false>(a, a.work[blockIdx.x], blockIdx.y, smem);
+    sweep_item<Real, TV, LINE, false, UNIF>(a, a.work[blockIdx.x], blockIdx.y, smem);
 }
 
 __device__ __forceinline__ int ld_acquire(const int *p)
@@ -663,7 +690,7 @@ __device__ bool wait_flag(const int *p, long long limit)
 // claimed in list order (stage-major), so every item's upwind dependencies
 // were claimed earlier by CTAs that are running: the waits always end unless
 // an error stopped a producer, and then they end at the poll limit.
-template <typename Real, int TV, int LINE>
+template <typename Real, int TV, int LINE, bool UNIF>
 __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSweepArgs b)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -697,7 +724,7 @@ __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSwee
         }
         __syncthreads();
         if (!s_go) break;
-        sweep_item<Real, TV, LINE, true>(sa, make_int4(o, bxr, byr, bzr), vg, smem);
+        sweep_item<Real, TV, LINE, true, UNIF>(sa, make_int4(o, bxr, byr, bzr), vg, smem);
         __syncthreads();
         if (threadIdx.x == 0 && it != b.skip_publish) {
             __threadfence();
@@ -707,82 +734,108 @@ __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSwee
     }
 }
 
-template <typename Real, int TV, int LINE>
+template <typename Real, int TV, int LINE, bool UNIF>
 cudaError_t launch_t(const SweepArgs &a, int n_items, int max_vg, cudaStream_t s)
 {
     using L = SmemLayout<Real, TV>;
     static size_t configured = 0;
     const size_t bytes = L::total(a.nxo_max);
     if (bytes > configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Real, TV, LINE>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Real, TV, LINE, UNIF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
         configured = bytes;
     }
     dim3 grid(n_items, max_vg);
-    sweep_kernel<Real, TV, LINE><<<grid, NT, bytes, s>>>(a);
+    sweep_kernel<Real, TV, LINE, UNIF><<<grid, NT, bytes, s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename Real, int TV>
 cudaError_t launch_line(const SweepArgs &a, int n_items, int max_vg, cudaStream_t s)
 {
-    if (a.line16) return launch_t<Real, TV, 16>(a, n_items, max_vg, s);
-    return launch_t<Real, TV, 0>(a, n_items, max_vg, s);
+    if (a.line16)
+        return a.uniform ? launch_t<Real, TV, 16, true>(a, n_items, max_vg, s)
+                         : launch_t<Real, TV, 16, false>(a, n_items, max_vg, s);
+    return a.uniform ? launch_t<Real, TV, 0, true>(a, n_items, max_vg, s)
+                     : launch_t<Real, TV, 0, false>(a, n_items, max_vg, s);
 }
 
-template <typename Real, int TV, int LINE>
+template <typename Real, int TV, int LINE, bool UNIF>
 cudaError_t launch_persistent_t(const BatchSweepArgs &b, int nxo_max, int grid, cudaStream_t s)
 {
     using L = SmemLayout<Real, TV>;
     static size_t configured = 0;
     const size_t bytes = L::total(nxo_max);
     if (bytes > configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE>,
+        cudaError_t e = cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE, UNIF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
         configured = bytes;
     }
-    sweep_persistent_kernel<Real, TV, LINE><<<grid, NT, bytes, s>>>(b);
+    sweep_persistent_kernel<Real, TV, LINE, UNIF><<<grid, NT, bytes, s>>>(b);
     return cudaGetLastError();
 }
 
-template <typename Real, int TV, int LINE>
+template <typename Real, int TV, int LINE, bool UNIF>
 int occupancy_t(size_t smem)
 {
     int n = 0;
-    if (cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE, UNIF>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_persistent_kernel<Real, TV, LINE>, NT, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_persistent_kernel<Real, TV, LINE, UNIF>, NT, smem) !=
         cudaSuccess)
         return 0;
     return n;
 }
 
-}  // namespace
-
-int sweep_persistent_occupancy(int precision, int tv, int line16, size_t smem)
+// Instantiation for (precision, velocities per thread, line specialisation,
+// uniform grid) chosen at run time.
+template <template <typename, int, int, bool> class F, typename... Args>
+auto dispatch(int precision, int tv, int line16, int uniform, Args &&...args)
 {
-    if (precision == 0) return line16 ? occupancy_t<double, 1, 16>(smem) : occupancy_t<double, 1, 0>(smem);
-    if (tv == 2) return line16 ? occupancy_t<float, 2, 16>(smem) : occupancy_t<float, 2, 0>(smem);
-    return line16 ? occupancy_t<float, 1, 16>(smem) : occupancy_t<float, 1, 0>(smem);
+#define KGS_CASES(R, T)                                                                \
+    if (line16)                                                                        \
+        return uniform ? F<R, T, 16, true>::run(args...) : F<R, T, 16, false>::run(args...); \
+    return uniform ? F<R, T, 0, true>::run(args...) : F<R, T, 0, false>::run(args...);
+    if (precision == 0) {
+        KGS_CASES(double, 1)
+    }
+    if (tv == 2) {
+        KGS_CASES(float, 2)
+    }
+    KGS_CASES(float, 1)
+#undef KGS_CASES
 }
 
-cudaError_t launch_sweep_persistent(int precision, int tv, int line16, const BatchSweepArgs &b, int nxo_max, int grid,
-                                    cudaStream_t s)
+template <typename Real, int TV, int LINE, bool UNIF>
+struct PersistentLaunch {
+    static cudaError_t run(const BatchSweepArgs &b, int nxo_max, int grid, cudaStream_t s)
+    {
+        return launch_persistent_t<Real, TV, LINE, UNIF>(b, nxo_max, grid, s);
+    }
+};
+
+template <typename Real, int TV, int LINE, bool UNIF>
+struct Occupancy {
+    static int run(size_t smem) { return occupancy_t<Real, TV, LINE, UNIF>(smem); }
+};
+
+}  // namespace
+
+int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem)
+{
+    return dispatch<Occupancy>(precision, tv, line16, uniform, smem);
+}
+
+cudaError_t launch_sweep_persistent(int precision, int tv, int line16, int uniform, const BatchSweepArgs &b,
+                                    int nxo_max, int grid, cudaStream_t s)
 {
     if (b.n_items == 0) return cudaSuccess;
-    if (precision == 0)
-        return line16 ? launch_persistent_t<double, 1, 16>(b, nxo_max, grid, s)
-                      : launch_persistent_t<double, 1, 0>(b, nxo_max, grid, s);
-    if (tv == 2)
-        return line16 ? launch_persistent_t<float, 2, 16>(b, nxo_max, grid, s)
-                      : launch_persistent_t<float, 2, 0>(b, nxo_max, grid, s);
-    return line16 ? launch_persistent_t<float, 1, 16>(b, nxo_max, grid, s)
-                  : launch_persistent_t<float, 1, 0>(b, nxo_max, grid, s);
+    return dispatch<PersistentLaunch>(precision, tv, line16, uniform, b, nxo_max, grid, s);
 }
 
 size_t sweep_smem_bytes(int precision, int tv, int nxo_max)

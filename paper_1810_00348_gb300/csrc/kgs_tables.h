@@ -41,6 +41,20 @@ struct HostTables {
     std::vector<int> stage_off, stage_n;
     std::vector<int4> work;
     size_t real_bytes() const { return precision == KGS_FP64 ? sizeof(double) : sizeof(float); }
+    // Equal cell widths along each axis: the sweep then takes the upwind
+    // coefficients a_d = abs(xi_d) / dx_d per velocity (sets a.uniform, a.rd0).
+    void set_uniformity(SweepArgs &a) const
+    {
+        auto same = [](const std::vector<double> &v) {
+            for (double x : v)
+                if (x != v[0]) return false;
+            return !v.empty();
+        };
+        a.uniform = same(rdx) && same(rdy) && same(rdz) ? 1 : 0;
+        a.rd0[0] = rdx.empty() ? 0.0 : rdx[0];
+        a.rd0[1] = rdy.empty() ? 0.0 : rdy[0];
+        a.rd0[2] = rdz.empty() ? 0.0 : rdz[0];
+    }
 };
 
 // Argument checks of kgs_setup (KGS_OK or KGS_EINVAL).
