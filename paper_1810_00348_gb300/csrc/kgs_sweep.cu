@@ -298,20 +298,6 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         return a.side_inflow[side] ? Real(1) : Real(a.rho_w[side * ncell + cell]);
     };
 
-    // z inflow of the block: the slice interior starts as slice k0-1.
-    for (int cl = 0; cl < SLICE; cl++) {
-        const int li = cl % BX, lj = cl / BX;
-        if (li >= ex || lj >= ey) continue;
-        const int x = GX(li), y = GY(lj), z = GZ(0);
-        const Real rw = zfirst ? wall_rho(sidez, CELL(x, y, z)) : Real(0);
-#pragma unroll
-        for (int m = 0; m < TV; m++) {
-            if (!ok[m]) continue;
-            const Real v = zfirst ? rw * mgz[m] : ld_face<COHERENT>(FZp + ((size_t)y * nx + x) * Nv + gv[m]);
-            slice[SL(li, lj) + t + m * NT] = v;
-        }
-    }
-
     // ---- prefetch registers: coefficients and halos of one slice ----
     Real pc[CPF];
     Real phx[BY][TV], phy[BX][TV];
@@ -367,6 +353,40 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         }
     };
     prefetch(0);
+
+    // z inflow of the block: the slice interior starts as slice k0-1.  A row
+    // of cells is loaded before it is stored, so a row's loads are in flight
+    // together.
+    if (zfirst) {
+        for (int lj = 0; lj < ey; lj++)
+            for (int li = 0; li < ex; li++) {
+                const Real rw = wall_rho(sidez, CELL(GX(li), GY(lj), GZ(0)));
+#pragma unroll
+                for (int m = 0; m < TV; m++)
+                    if (ok[m]) slice[SL(li, lj) + t + m * NT] = rw * mgz[m];
+            }
+    } else {
+        const long long sx = px ? (long long)Nv : -(long long)Nv;
+        for (int lj = 0; lj < ey; lj++) {
+            const Real *fi = FZp + ((size_t)GY(lj) * nx + GX(0)) * Nv;
+            Real v[BX][TV];
+#pragma unroll
+            for (int li = 0; li < BX; li++) {
+                if (li >= ex) break;
+#pragma unroll
+                for (int m = 0; m < TV; m++)
+                    v[li][m] = ok[m] ? ld_face<COHERENT>(fi + li * sx + (long long)gv[m]) : Real(0);
+            }
+#pragma unroll
+            for (int li = 0; li < BX; li++) {
+                if (li >= ex) break;
+#pragma unroll
+                for (int m = 0; m < TV; m++)
+                    if (ok[m]) slice[SL(li, lj) + t + m * NT] = v[li][m];
+            }
+        }
+    }
+
 
     for (int lk = 0; lk < ez; lk++) {
         const int z = GZ(lk);
