@@ -270,8 +270,9 @@ void kgs_batch_destroy(kgs_batch *b);
  * The FP32 form of the iteration settles into rounding noise around its
  * fixed point, so its residual stops falling at a floor (about 3e-5 on the
  * cavity's spanwise momentum).  kgs_solve runs mixed iterations in chunks of
- * 5 while the residual keeps falling (below 0.9 x its best value within
- * two chunks), then continues in FP64 from the mixed state (macros, wall
+ * 5 while the residual keeps falling (below 0.9 x its best value within two
+ * chunks once it is below 1e-3, within twenty chunks above), then continues
+ * in FP64 from the mixed state (macros, wall
  * densities and mass target carried over as by kgs_save / kgs_load) until
  * the residual is below tol or max_iters iterations ran in all.
  * initial: host [8][nz][ny][nx] or NULL (uniform state).  macros_out: host,

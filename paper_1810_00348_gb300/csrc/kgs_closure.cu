@@ -95,16 +95,18 @@ struct FFSum {
 };
 
 // Closure of one outer iteration for CLOSE_CELLS cells per block: thread
-// (slot q, cell) sums partial q of its cell over all velocity groups in group
-// order (16 threads per cell keep many loads in flight), then one thread per
-// cell turns the sums into the macroscopic fields and wall densities.
+// (cell, slot q) sums partial q of its cell over all velocity groups in group
+// order (a warp reads the contiguous partials of two cells per group; 16
+// threads per cell keep many loads in flight), then one thread per cell turns
+// the sums into the macroscopic fields and wall densities.
 template <typename Real>
 __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseArgs a)
 {
     constexpr int NS = 13 + 6;  // 13 sums about U^n, incoming flux per side
     __shared__ double sS[CLOSE_CELLS][NS];
     const size_t ncell = a.ncell;
-    const int cl = threadIdx.x % CLOSE_CELLS, q = threadIdx.x / CLOSE_CELLS;
+    {
+    const int cl = threadIdx.x / NPART, q = threadIdx.x % NPART;
     const size_t c = (size_t)blockIdx.x * CLOSE_CELLS + cl;
     const bool live = c < ncell && !(a.solid && a.solid[c]);
     if (live) {
@@ -112,10 +114,10 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
         double sum, f_minus, f_plus;
         if (sizeof(Real) == 8) {
             sum = f_minus = f_plus = 0.0;
-            const double *pp = static_cast<const double *>(a.part) + (size_t)q * ncell + c;
+            const double *pp = static_cast<const double *>(a.part) + c * NPART + q;
 #pragma unroll 4
             for (int g = 0; g < a.n_vg; g++) {
-                const double v = pp[(size_t)g * NPART * ncell];
+                const double v = pp[(size_t)g * ncell * NPART];
                 if (q < P_FX)
                     sum += v;
                 else if ((a.vg_oct[g] >> axis) & 1)  // the wall ahead of the group's octant
@@ -128,10 +130,10 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
             // summed as float-float numbers (hi + lo, hi updated by an error-
             // free two-sum) on the FP32 pipe and widened once at the end
             FFSum acc[2];
-            const float2 *pp = static_cast<const float2 *>(a.part) + (size_t)q * ncell + c;
-#pragma unroll 4
-            for (int g = 0; g < a.n_vg; g++) {
-                const float2 e = pp[(size_t)g * NPART * ncell];
+            const float2 *pp = static_cast<const float2 *>(a.part) + c * NPART + q;
+#pragma unroll 16
+            for (int g = 0; g < a.n_vg; g++) {  // 16 loads in flight per thread
+                const float2 e = pp[(size_t)g * ncell * NPART];
                 const int side = q < P_FX ? 0 : ((a.vg_oct[g] >> axis) & 1);
                 acc[side].add(e.x, e.y);
             }
@@ -145,8 +147,13 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
             sS[cl][13 + 2 * axis + 1] = f_plus;
         }
     }
+    }
     __syncthreads();
+    // one thread per cell from here on
     if (threadIdx.x >= CLOSE_CELLS) return;
+    const int cl = threadIdx.x;
+    const size_t c = (size_t)blockIdx.x * CLOSE_CELLS + cl;
+    const bool live = c < ncell && !(a.solid && a.solid[c]);
     double mass = 0.0;
     if (live) {
         const double *S = sS[cl];

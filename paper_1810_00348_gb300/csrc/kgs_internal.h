@@ -70,7 +70,7 @@ struct SweepArgs {
     const void *mtab;             // Real[MT_ROWS][Nv]: unit wall Maxwellians, free stream
     int side_inflow[6];           // domain side s is a free-stream boundary
     void *FX, *FY, *FZ;           // face planes: [nz*ny][Nv], [nz*nx][Nv], [ny*nx][Nv]
-    void *part;                   // [n_vg][NPART][ncell]: double (FP64 path) or float2 (s, c)
+    void *part;                   // [n_vg][ncell][NPART]: double (FP64 path) or float2 (s, c)
                                   // with value s - c (FP32 path, Kahan pair)
     unsigned long long ncell;
     int line16;                   // every octant has x-lines of 16 nodes (specialised moment loop)
@@ -143,7 +143,7 @@ struct CloseArgs {
     unsigned long long ncell;
     int n_vg;
     const int *vg_oct;            // [n_vg] octant of each velocity group
-    const void *part;             // [n_vg][NPART][ncell], see SweepArgs::part
+    const void *part;             // [n_vg][ncell][NPART], see SweepArgs::part
     const void *coef;             // sweep-precision coefficients (U centre)
     int precision;
     const double *mac;            // [8][ncell] step n

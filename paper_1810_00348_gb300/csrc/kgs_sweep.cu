@@ -646,14 +646,18 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
             }
             __syncthreads();
             if (vp == 0 && valid) {
-                Out *pp = static_cast<Out *>(a.part) + (size_t)vgid * NPART * ncell + CELL(GX(li), GY(lj), z);
+                // the cell's NPART partials are contiguous (128 bytes)
+                Out *pp = static_cast<Out *>(a.part) + ((size_t)vgid * ncell + CELL(GX(li), GY(lj), z)) * NPART;
 #pragma unroll
-                for (int q = 0; q < NPART; q++) {
+                for (int q = 0; q < NPART; q += 2) {
                     if constexpr (sizeof(Real) == 8) {
-                        pp[(size_t)q * ncell] = S[q].value() + red[q * SLICE + cl];
+                        *reinterpret_cast<double2 *>(pp + q) = make_double2(S[q].value() + red[q * SLICE + cl],
+                                                                            S[q + 1].value() + red[(q + 1) * SLICE + cl]);
                     } else {
-                        const float2 o2 = red[q * SLICE + cl];
-                        pp[(size_t)q * ncell] = pair_add(S[q].s, S[q].c, o2.x, o2.y);
+                        const float2 o0 = red[q * SLICE + cl], o1 = red[(q + 1) * SLICE + cl];
+                        const float2 r0 = pair_add(S[q].s, S[q].c, o0.x, o0.y);
+                        const float2 r1 = pair_add(S[q + 1].s, S[q + 1].c, o1.x, o1.y);
+                        *reinterpret_cast<float4 *>(pp + q) = make_float4(r0.x, r0.y, r1.x, r1.y);
                     }
                 }
             }

@@ -210,3 +210,87 @@ def iterations_to(prob: inputs.Problem, initial: Optional[np.ndarray], precision
     dt = time.perf_counter() - t0
     kgs.kgs_destroy(ctx)
     return n, dt, res, rc
+
+
+def main(argv=None):
+    """Train the network on solver-generated cavities and report the
+    iterations and time to a residual of 1e-6 on held-out cavities, from the
+    uniform state (plain FP64; mixed then FP64) and from the guess.
+
+        python -m paper_1810_00348_gb300.surrogate --samples 512 --steps 3000
+    """
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--samples", type=int, default=512, help="training cavities (seed 1)")
+    ap.add_argument("--cells", type=int, default=16)
+    ap.add_argument("--vels", type=int, default=16)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--kn", default="0.05,0.2,0.5", help="held-out Knudsen numbers")
+    ap.add_argument("--lids", default="0.1,0.25", help="held-out lid speeds")
+    ap.add_argument("--save", default="", help="write the trained parameters (float32) to this file")
+    ap.add_argument("--forward-only", type=int, default=0,
+                    help="only time forward passes of the untrained network on one N^3 volume and exit")
+    args = ap.parse_args(argv)
+    kgs.load()
+    if args.forward_only:
+        n = args.forward_only
+        s = Surrogate(seed=0)
+        shape = (1, n, n, n)
+        x = torch.randn(shape + (N_FEATURES,), device="cuda")
+        y = torch.empty(shape + (N_FIELDS,), device="cuda")
+        ms = []
+        for _ in range(4):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            kgs.kgs_net_forward(s.net, x.data_ptr(), shape, y.data_ptr())
+            ms.append((time.perf_counter() - t1) * 1e3)
+        print(json.dumps({"forward_ms": ms[1:], "voxels": n ** 3}))
+        return
+    t0 = time.perf_counter()
+    samples = make_samples(draw_cavities(args.samples, seed=1, cells=args.cells, vels=args.vels),
+                           precision=kgs.KGS_FP64, tol=1e-6, max_iters=5000)
+    t_data = time.perf_counter() - t0
+    s = Surrogate(seed=0)
+    t0 = time.perf_counter()
+    losses = s.train(samples, steps=args.steps, batch=args.batch, lr=args.lr, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    if args.save:
+        kgs.kgs_net_get(s.net, 0).tofile(args.save)
+    cases = []
+    for kn in [float(v) for v in args.kn.split(",")]:
+        for lid in [float(v) for v in args.lids.split(",")]:
+            p = inputs.cavity(args.cells, args.vels, Kn=kn, lid=lid)
+            n_fp64, t_fp64, _, _ = iterations_to(p, None, kgs.KGS_FP64, 1e-6, 5000)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, _, nm, nd, _ = kgs.kgs_solve(p, None, 1e-6, 5000)
+            t_mixed = time.perf_counter() - t1
+            t1 = time.perf_counter()
+            _, coarse, cm, cd, _ = kgs.kgs_solve(coarse_problem(p), None, 1e-6, 5000)
+            guess, n_bad = s.guess(p, coarse)
+            _, _, sm, sd, _ = kgs.kgs_solve(p, guess, 1e-6, 5000)
+            torch.cuda.synchronize()
+            t_sur = time.perf_counter() - t1
+            _, up = upsample(p, coarse)
+            n_up, _, _, _ = iterations_to(p, up.cpu().numpy(), kgs.KGS_FP64, 1e-6, 5000)
+            n_nn, _, _, _ = iterations_to(p, guess, kgs.KGS_FP64, 1e-6, 5000) if guess is not None else (None,) * 4
+            cases.append({"Kn": kn, "lid": lid,
+                          "fp64_iterations": {"uniform": n_fp64, "upsampled_coarse": n_up, "surrogate": n_nn},
+                          "seconds": {"fp64_uniform": t_fp64, "mixed_fp64_uniform": t_mixed,
+                                      "mixed_fp64_surrogate_incl_coarse": t_sur},
+                          "mixed_fp64_iterations": {"uniform": [nm, nd], "surrogate": [sm, sd],
+                                                    "coarse": [cm, cd]},
+                          "guess_rejected": guess is None})
+    print(json.dumps({"samples": len(samples), "cells": args.cells, "vels": args.vels, "data_s": t_data,
+                      "train_s": t_train, "steps": args.steps, "loss_first": float(np.mean(losses[:20])),
+                      "loss_last": float(np.mean(losses[-20:])), "params": s.num_params(), "cases": cases},
+                     indent=1))
+
+
+if __name__ == "__main__":
+    main()
