@@ -11,10 +11,13 @@
 // positions of an output row segment are 8 consecutive 16-byte rows (one
 // 8 x 16 B core matrix) and the 16 y rows and the channel octets are fixed
 // strides.  Each tap is then C/16 MMAs of 128 x N x 16 reading shifted
-// windows of the same halo; no im2col copy is made.  Halo and weights move
-// with asynchronous copies (cp.async); the weights of a tap (N x C) rotate
-// through three buffers: tap t+2 is fetched while the tensor core works on
-// tap t, once a commit barrier shows that tap t-1 has released its buffer.  The epilogue reads the accumulator with tcgen05.ld (warp w owns
+// windows of the same halo; no im2col copy is made.  The halo moves with
+// cp.async.  The weights, packed beforehand so that a tap is one contiguous
+// block in the layout the MMA reads, move with one bulk copy per tap into a
+// ring of four buffers.  Two threads drive the pipeline without CTA-wide
+// barriers: a producer issues the copy of tap t once the MMAs of tap t-4 have
+// released its buffer (commit barrier), and an issuer starts the MMAs of tap
+// t once its copy has landed (transaction barrier).  The epilogue reads the accumulator with tcgen05.ld (warp w owns
 // TMEM lanes 32w..32w+31 = output rows) and applies bias + ReLU, bias only,
 // or the ReLU mask of the backward pass.
 //
@@ -32,7 +35,7 @@ constexpr int TX = 8, TY = 16;                 // output patch: 128 voxels = 128
 constexpr int HX = TX + 2, HY = TY + 2, HZ = 3;  // input halo of the patch
 constexpr int THREADS = 128;
 constexpr int TMEM_COLS = 128;                 // >= N, a power of two
-constexpr int NBUF = 3;                        // weight buffers: taps t, t+1, t+2 in flight
+constexpr int NBUF = 4;                        // weight buffers: up to four taps in flight
 constexpr long long WAIT_POLLS = 1ll << 20;    // try_wait polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -86,6 +89,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory; completion is counted on barrier `bar`.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -118,34 +135,60 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// Weights W[t][co][ci] -> packed[t][ci/8][co][8]: each tap becomes one
+// contiguous block in exactly the shared-memory layout the MMA reads, so it
+// moves with a single bulk copy.
+__global__ void pack_w_kernel(const uint4 *__restrict__ w, int cout_p, int c8n, uint4 *__restrict__ wpk)
+{
+    const size_t per = (size_t)cout_p * c8n;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 27 * per) return;
+    const size_t t = i / per, r = i % per;
+    const int co = (int)(r / c8n), c8 = (int)(r % c8n);
+    wpk[t * per + (size_t)c8 * cout_p + co] = w[i];
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
-    conv_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ w,
+    conv_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wpk,
                    const float *__restrict__ bias, void *out, const __nv_bfloat16 *__restrict__ gate, ConvDims dm,
                    int *err)
 {
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ __align__(8) uint64_t mbar[NBUF];
+    __shared__ __align__(8) uint64_t full_bar[NBUF], empty_bar[NBUF], done_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail, s_last;  // a wait gave up; last tap whose MMAs were committed
 
     const int C8 = dm.cin_p / 8, cout_p = dm.cout_p;
     const size_t halo_bytes = (size_t)HZ * HY * C8 * HX * 16;
-    const size_t w_bytes = (size_t)C8 * cout_p * 16;
+    const uint32_t w_bytes = (uint32_t)C8 * cout_p * 16;
     unsigned char *halo = sm;
     unsigned char *wbuf = sm + halo_bytes;
     const int tiles_x = (dm.W + TX - 1) / TX;
     const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
     const int z = blockIdx.y, b = blockIdx.z;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    auto bar = [&](int t) { return smem_u32(&mbar[t % NBUF]); };  // commit barrier of tap t
-    auto parity = [](int t) { return (uint32_t)((t / NBUF) & 1); };
+    auto full = [&](int t) { return smem_u32(&full_bar[t % NBUF]); };    // weights of tap t landed
+    auto empty = [&](int t) { return smem_u32(&empty_bar[t % NBUF]); };  // MMAs of tap t done
+    auto use = [](int t) { return (uint32_t)((t / NBUF) & 1); };         // phase parity of tap t's use
+    const uint32_t halo_a = smem_u32(halo), w_a = smem_u32(wbuf);
+    volatile int *fail = &s_fail;  // written by the two pipeline threads
+    auto issue_w = [&](int t) {  // bulk copy of tap t into buffer t % NBUF
+        mbar_expect_tx(full(t), w_bytes);
+        bulk_copy(w_a + (uint32_t)(t % NBUF) * w_bytes, wpk + (size_t)t * cout_p * dm.cin_p, w_bytes, full(t));
+    };
 
     if (threadIdx.x == 0) {
-        for (int q = 0; q < NBUF; q++) mbar_init(smem_u32(&mbar[q]), 1);
+        for (int q = 0; q < NBUF; q++) {
+            mbar_init(smem_u32(&full_bar[q]), 1);
+            mbar_init(smem_u32(&empty_bar[q]), 1);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
         s_last = -1;
+        // the first NBUF taps need no free buffer: start them now
+        for (int t = 0; t < NBUF; t++) issue_w(t);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -156,7 +199,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     // input halo: element (hx, hy, hz, channel octet c8) at ((hz*HY + hy)*C8 + c8)*HX + hx
     const size_t vol = (size_t)dm.D * dm.H * dm.W;
-    const uint32_t halo_a = smem_u32(halo), w_a = smem_u32(wbuf);
     for (int i = threadIdx.x; i < HZ * HY * HX * C8; i += THREADS) {
         const int c8 = i % C8, r = i / C8;
         const int hx = r % HX, hy = (r / HX) % HY, hz = r / (HX * HY);
@@ -167,58 +209,51 @@ __global__ void __launch_bounds__(THREADS, 1)
         cp_async16(halo_a + (uint32_t)(((hz * HY + hy) * C8 + c8) * HX + hx) * 16, src, valid);
     }
     cp_async_commit();
-    // weights of tap t into buffer t % NBUF: element (co, octet c8) at c8*cout_p + co
-    auto load_w = [&](int t) {
-        const __nv_bfloat16 *src = w + (size_t)t * cout_p * dm.cin_p;
-        const uint32_t dst = w_a + (uint32_t)((t % NBUF) * w_bytes);
-        for (int i = threadIdx.x; i < cout_p * C8; i += THREADS) {
-            const int c8 = i % C8, co = i / C8;
-            cp_async16(dst + (uint32_t)(c8 * cout_p + co) * 16, src + (size_t)co * dm.cin_p + c8 * 8, true);
-        }
-        cp_async_commit();
-    };
-    load_w(0);
-    load_w(1);
-    const uint32_t idesc = instr_desc(128, cout_p);
-    const uint32_t a_lbo = HX * 16, a_sbo = (uint32_t)C8 * HX * 16;
-    const uint32_t b_lbo = (uint32_t)cout_p * 16, b_sbo = 8 * 16;
+    cp_async_wait<0>();
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
-    for (int t = 0; t < 27; t++) {
-        // the copies of the halo and of tap t have landed (tap t+1 may be in flight)
-        if (t < 26)
-            cp_async_wait<1>();
-        else
-            cp_async_wait<0>();
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
-        if (threadIdx.x == 0 && !s_fail) {
-            const uint32_t tmem = tmem_base;
+    if (threadIdx.x == 0) {
+        // producer: tap t reuses the buffer of tap t - NBUF once its MMAs are done
+        for (int t = NBUF; t < 27; t++) {
+            if (*fail || !mbar_wait(empty(t - NBUF), use(t - NBUF))) {
+                *fail = 1;
+                break;
+            }
+            issue_w(t);
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer: C/16 MMAs of 128 x N x 16 per tap, accumulating in TMEM
+        const uint32_t tmem = tmem_base;
+        const uint32_t idesc = instr_desc(128, cout_p);
+        const uint32_t a_lbo = HX * 16, a_sbo = (uint32_t)C8 * HX * 16;
+        const uint32_t b_lbo = (uint32_t)cout_p * 16, b_sbo = 8 * 16;
+        for (int t = 0; t < 27; t++) {
+            if (*fail || !mbar_wait(full(t), use(t))) {
+                *fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
             for (int kc = 0; kc < C8 / 2; kc++) {
                 const uint64_t a = smem_desc(halo_a + (uint32_t)((((kz * HY + ky) * C8 + 2 * kc) * HX + kx) * 16),
                                              a_lbo, a_sbo);
                 const uint64_t bd =
-                    smem_desc(w_a + (uint32_t)((t % NBUF) * w_bytes + (size_t)2 * kc * cout_p * 16), b_lbo, b_sbo);
+                    smem_desc(w_a + (uint32_t)(t % NBUF) * w_bytes + (uint32_t)(2 * kc * cout_p * 16), b_lbo, b_sbo);
                 tc_mma(tmem, a, bd, idesc, (t | kc) != 0);
             }
-            tc_commit(bar(t));
+            tc_commit(empty(t));
             s_last = t;
         }
-        if (t + 2 < 27) {
-            // buffer (t+2) % NBUF was read by tap t-1: wait for its commit
-            if (t >= 1 && !s_fail && !mbar_wait(bar(t - 1), parity(t - 1))) s_fail = 1;
-            load_w(t + 2);
-        }
+        tc_commit(smem_u32(&done_bar));  // all MMAs issued by this thread
     }
-    // all MMAs of the CTA are complete once the last commit has arrived (on
-    // failure: the last commit that was made, so that no MMA still writes the
-    // tensor memory freed below)
+    // all MMAs of the CTA are complete once the done barrier has fired
+    const bool done = mbar_wait(smem_u32(&done_bar), 0);
     __syncthreads();
-    const uint32_t tmem = tmem_base;
     const int last = s_last;
-    const bool done = last >= 0 && mbar_wait(bar(last), parity(last));
+    const uint32_t tmem = tmem_base;
     tc_fence_after();
     if (!done || s_fail || last != 26) {
         if (threadIdx.x == 0) atomicExch(err, 1);
@@ -270,28 +305,33 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 template <int MODE>
-cudaError_t launch(const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
+cudaError_t launch(const __nv_bfloat16 *in, const __nv_bfloat16 *wpk, const float *bias, void *out,
                    const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
 {
     const size_t smem = (size_t)HZ * HY * (dm.cin_p / 8) * HX * 16 + NBUF * (size_t)(dm.cin_p / 8) * dm.cout_p * 16;
     cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int tiles = ((dm.W + TX - 1) / TX) * ((dm.H + TY - 1) / TY);
-    conv_tc_kernel<MODE><<<dim3(tiles, dm.D, dm.B), THREADS, smem, s>>>(in, w, bias, out, gate, dm, err);
+    conv_tc_kernel<MODE><<<dim3(tiles, dm.D, dm.B), THREADS, smem, s>>>(in, wpk, bias, out, gate, dm, err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t conv_tc(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
-                    const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
+cudaError_t conv_tc(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, __nv_bfloat16 *wpk, const float *bias,
+                    void *out, const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
 {
     if (dm.cin_p % 16 || dm.cout_p % 16 || dm.cin_p < 16 || dm.cout_p < 16 || dm.cin_p > 112 || dm.cout_p > 112)
         return cudaErrorInvalidValue;
+    const size_t n16 = (size_t)27 * dm.cout_p * (dm.cin_p / 8);
+    pack_w_kernel<<<(unsigned)((n16 + 255) / 256), 256, 0, s>>>(reinterpret_cast<const uint4 *>(w), dm.cout_p,
+                                                                 dm.cin_p / 8, reinterpret_cast<uint4 *>(wpk));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     switch (mode) {
-    case 0: return launch<0>(in, w, bias, out, gate, dm, err, s);
-    case 1: return launch<1>(in, w, bias, out, gate, dm, err, s);
-    default: return launch<2>(in, w, bias, out, gate, dm, err, s);
+    case 0: return launch<0>(in, wpk, bias, out, gate, dm, err, s);
+    case 1: return launch<1>(in, wpk, bias, out, gate, dm, err, s);
+    default: return launch<2>(in, wpk, bias, out, gate, dm, err, s);
     }
 }
 

@@ -367,10 +367,10 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 size_t wgrad_smem(int cin_p, int cout_p) { return (size_t)HV * (cin_p + 8) * 2 + (size_t)TV_ * (cout_p + 8) * 2; }
 
-cudaError_t run_conv(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
-                     const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
+cudaError_t run_conv(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, __nv_bfloat16 *wpk,
+                     const float *bias, void *out, const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
 {
-    return kgs::nn::conv_tc(mode, in, w, bias, out, gate, dm, err, s);
+    return kgs::nn::conv_tc(mode, in, w, wpk, bias, out, gate, dm, err, s);
 }
 
 }  // namespace
@@ -388,6 +388,7 @@ struct kgs_net {
     float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;  // FP32 master, grad, Adam moments
     __nv_bfloat16 *pb = nullptr;        // bf16 copy of the parameters
     __nv_bfloat16 *wt = nullptr;        // transposed weights of one layer (data gradient)
+    __nv_bfloat16 *wpk = nullptr;       // one layer's weights packed for the convolution kernel
     long long step = 0;
     // activation storage for the current shape
     int B = 0, D = 0, H = 0, W = 0;
@@ -475,9 +476,9 @@ int forward(kgs_net *n, const float *x)
         const __nv_bfloat16 *w = n->pb + n->w_off[l];
         const float *bias = n->p + n->b_off[l];
         if (l < n->L - 1)
-            NN_CHECK(run_conv(0, n->act[l], w, bias, n->act[l + 1], nullptr, dims(n, l), n->d_err, s));
+            NN_CHECK(run_conv(0, n->act[l], w, n->wpk, bias, n->act[l + 1], nullptr, dims(n, l), n->d_err, s));
         else
-            NN_CHECK(run_conv(1, n->act[l], w, bias, n->out, nullptr, dims(n, l), n->d_err, s));
+            NN_CHECK(run_conv(1, n->act[l], w, n->wpk, bias, n->out, nullptr, dims(n, l), n->d_err, s));
     }
     return KGS_OK;
 }
@@ -515,7 +516,7 @@ int backward(kgs_net *n)
         transpose_w_kernel<<<nblk(per, 256), 256, 0, s>>>(n->pb + n->w_off[l], dm.cout_p, dm.cin_p, n->wt);
         NN_CHECK(cudaGetLastError());
         const ConvDims db{n->B, n->D, n->H, n->W, dm.cout_p, dm.cin_p};
-        NN_CHECK(run_conv(2, gcur, n->wt, nullptr, gnext, n->act[l], db, n->d_err, s));
+        NN_CHECK(run_conv(2, gcur, n->wt, n->wpk, nullptr, gnext, n->act[l], db, n->d_err, s));
         std::swap(gcur, gnext);
     }
     return KGS_OK;
@@ -577,7 +578,7 @@ int kgs_net_create(kgs_net **out, int n_layers, const int *channels, unsigned lo
     };
     if (cudaMalloc(&n->p, off * 4) != cudaSuccess || cudaMalloc(&n->g, off * 4) != cudaSuccess ||
         cudaMalloc(&n->m1, off * 4) != cudaSuccess || cudaMalloc(&n->m2, off * 4) != cudaSuccess ||
-        cudaMalloc(&n->pb, off * 2) != cudaSuccess || cudaMalloc(&n->wt, wmax * 2) != cudaSuccess ||
+        cudaMalloc(&n->pb, off * 2) != cudaSuccess || cudaMalloc(&n->wt, wmax * 2) != cudaSuccess || cudaMalloc(&n->wpk, wmax * 2) != cudaSuccess ||
         cudaMallocHost(&n->h_loss, sizeof(float)) != cudaSuccess || cudaMalloc(&n->d_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&n->h_err, sizeof(int)) != cudaSuccess)
         return fail(KGS_ENOMEM);
@@ -764,6 +765,7 @@ void kgs_net_destroy(kgs_net *n)
         if (b) cudaFree(b);
     if (n->pb) cudaFree(n->pb);
     if (n->wt) cudaFree(n->wt);
+    if (n->wpk) cudaFree(n->wpk);
     if (n->h_loss) cudaFreeHost(n->h_loss);
     if (n->d_err) cudaFree(n->d_err);
     if (n->h_err) cudaFreeHost(n->h_err);

@@ -16,10 +16,11 @@ struct ConvDims {
 //   mode 0: out = relu(acc + bias) as bf16
 //   mode 1: out = acc + bias as FP32
 //   mode 2: out = acc * (gate > 0) as bf16 (gate: bf16, same layout as out)
-// w: [27][cout_p][cin_p] bf16.  err: device word set to 1 if a bounded wait
-// inside the kernel gave up (the output is then incomplete).
-cudaError_t conv_tc(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, const float *bias, void *out,
-                    const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s);
+// w: [27][cout_p][cin_p] bf16; wpk: scratch of the same size that receives
+// the weights repacked for the kernel.  err: device word set to 1 if a
+// bounded wait inside the kernel gave up (the output is then incomplete).
+cudaError_t conv_tc(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, __nv_bfloat16 *wpk, const float *bias,
+                    void *out, const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s);
 
 }  // namespace nn
 }  // namespace kgs
