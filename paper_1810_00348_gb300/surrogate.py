@@ -89,6 +89,18 @@ def upsample(prob: inputs.Problem, coarse: np.ndarray, kn: Optional[float] = Non
     return x, up
 
 
+def coarse_solution(prob: inputs.Problem, factor: int = 2, tol: float = 1e-4, max_iters: int = 1000) -> np.ndarray:
+    """Macroscopic fields of `prob` on the grid `factor` times coarser, from
+    the mixed-precision iteration stopped at residual `tol` (the network's
+    input needs no tighter solution; 1e-4 lies above the mixed path's noise
+    floor).  Returns [8, nz/f, ny/f, nx/f]."""
+    c = kgs.kgs_setup(coarse_problem(prob, factor), precision=kgs.KGS_MIXED, tol=tol, max_iters=max_iters)
+    kgs.kgs_iterate(c, 0)
+    m = kgs.kgs_moments(c)
+    kgs.kgs_destroy(c)
+    return m
+
+
 @dataclasses.dataclass
 class Sample:
     prob: inputs.Problem
@@ -232,6 +244,10 @@ def main(argv=None):
     ap.add_argument("--kn", default="0.05,0.2,0.5", help="held-out Knudsen numbers")
     ap.add_argument("--lids", default="0.1,0.25", help="held-out lid speeds")
     ap.add_argument("--save", default="", help="write the trained parameters (float32) to this file")
+    ap.add_argument("--eval-cells", type=int, default=0,
+                    help="also evaluate on held-out cavities of this size (cells per side; 0 = training size)")
+    ap.add_argument("--eval-vels", type=int, default=0, help="velocities per side of the extra evaluation")
+    ap.add_argument("--eval-kn", default="0.5", help="Knudsen numbers of the extra evaluation")
     ap.add_argument("--forward-only", type=int, default=0,
                     help="only time forward passes of the untrained network on one N^3 volume and exit")
     args = ap.parse_args(argv)
@@ -271,7 +287,7 @@ def main(argv=None):
             _, _, nm, nd, _ = kgs.kgs_solve(p, None, 1e-6, 5000)
             t_mixed = time.perf_counter() - t1
             t1 = time.perf_counter()
-            _, coarse, cm, cd, _ = kgs.kgs_solve(coarse_problem(p), None, 1e-6, 5000)
+            coarse = coarse_solution(p)
             guess, n_bad = s.guess(p, coarse)
             _, _, sm, sd, _ = kgs.kgs_solve(p, guess, 1e-6, 5000)
             torch.cuda.synchronize()
@@ -283,12 +299,34 @@ def main(argv=None):
                           "fp64_iterations": {"uniform": n_fp64, "upsampled_coarse": n_up, "surrogate": n_nn},
                           "seconds": {"fp64_uniform": t_fp64, "mixed_fp64_uniform": t_mixed,
                                       "mixed_fp64_surrogate_incl_coarse": t_sur},
-                          "mixed_fp64_iterations": {"uniform": [nm, nd], "surrogate": [sm, sd],
-                                                    "coarse": [cm, cd]},
+                          "mixed_fp64_iterations": {"uniform": [nm, nd], "surrogate": [sm, sd]},
                           "guess_rejected": guess is None})
+    extra = []
+    if args.eval_cells:
+        # a larger grid than the training one: the network was trained at
+        # another cell size, so the guess may help less (or be rejected)
+        for kn in [float(v) for v in args.eval_kn.split(",")]:
+            p = inputs.cavity(args.eval_cells, args.eval_vels or args.vels, Kn=kn, lid=0.16)
+            n_fp64, t_fp64, _, rc_f = iterations_to(p, None, kgs.KGS_FP64, 1e-6, 400)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            rc_m, _, nm, nd, _ = kgs.kgs_solve(p, None, 1e-6, 400)
+            t_mixed = time.perf_counter() - t1
+            t1 = time.perf_counter()
+            coarse = coarse_solution(p)
+            guess, n_bad = s.guess(p, coarse)
+            rc_s, _, sm, sd, _ = kgs.kgs_solve(p, guess, 1e-6, 400)
+            torch.cuda.synchronize()
+            t_sur = time.perf_counter() - t1
+            extra.append({"cells": args.eval_cells, "vels": args.eval_vels or args.vels, "Kn": kn, "lid": 0.16,
+                          "fp64_uniform": {"iterations": n_fp64, "s": t_fp64, "rc": rc_f},
+                          "mixed_fp64_uniform": {"iterations": [nm, nd], "s": t_mixed, "rc": rc_m},
+                          "mixed_fp64_surrogate": {"iterations": [sm, sd], "s": t_sur, "rc": rc_s,
+                                                   "guess_rejected": guess is None}})
     print(json.dumps({"samples": len(samples), "cells": args.cells, "vels": args.vels, "data_s": t_data,
                       "train_s": t_train, "steps": args.steps, "loss_first": float(np.mean(losses[:20])),
-                      "loss_last": float(np.mean(losses[-20:])), "params": s.num_params(), "cases": cases},
+                      "loss_last": float(np.mean(losses[-20:])), "params": s.num_params(), "cases": cases,
+                      "larger_grid": extra},
                      indent=1))
 
 
