@@ -112,8 +112,10 @@ typedef struct {
  *                mass stays at its initial value (closed cavities, Section 3.4).
  *   max_iters, tol  used by kgs_iterate(n_iters <= 0): iterate until the
  *                residual is below tol or max_iters iterations have run.
- *   v_per_cta    discrete velocities per thread block (0 = default for the
- *                precision); block_z cells per sweep block along z (0 = default).
+ *   v_per_cta    discrete velocities per thread block: 0 (default for the
+ *                precision, 256 for KGS_MIXED, 128 for KGS_FP64), 128, or 256
+ *                (KGS_MIXED only); block_z cells per sweep block along z
+ *                (0 = default, 32).
  *   stream       cudaStream_t to launch on (NULL = legacy default stream). */
 typedef struct {
     int precision;
@@ -132,7 +134,7 @@ typedef struct {
     long long n_fluid;          /* fluid cells                                     */
     long long phase_points;     /* n_fluid * nvel: updates per outer iteration     */
     int iteration;              /* outer iterations done since setup / load        */
-    int n_stages;               /* sweep launches per outer iteration              */
+    int n_stages;               /* wavefront stages of the sweep (all in one launch) */
     int v_per_cta, block_z, precision;
     size_t device_bytes;        /* device memory held by the context               */
     double last_residual;
@@ -161,8 +163,12 @@ int kgs_set_initial(kgs_ctx *ctx, const double *macros);
  * (may be NULL) the last residual (Section 4.1 reading: the largest relative
  * L2 change of rho, rho Ux, rho Uy, rho Uz, rho E over fluid cells, each
  * denominator floored at 1e-8 ||rho||_2).
+ * Each iteration is one persistent sweep launch over the context's work items
+ * (octant, velocity group, 8x8xblock_z block) in wavefront order; a thread
+ * block waits with a bounded poll for the three upwind blocks of its item.
  * Returns KGS_OK, KGS_NOTCONVERGED (n_iters <= 0 only), KGS_EDIVERGED
- * (the state is left at the offending iterate), KGS_ECUDA. */
+ * (the state is left at the offending iterate), KGS_ETIMEOUT (a bounded wait
+ * gave up; the iteration's results are discarded), KGS_ECUDA. */
 int kgs_iterate(kgs_ctx *ctx, int n_iters, int *done, double *residual);
 
 /* Copy the current macroscopic fields to host memory out[8*nz*ny*nx]
