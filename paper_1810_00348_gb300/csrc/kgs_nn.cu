@@ -6,15 +6,14 @@
 // every product is accumulated in FP32.  A layer is a 3x3x3 convolution with
 // zero padding, bias, and ReLU except on the last layer.  As a GEMM it is
 // out[v][co] = sum_{t, ci} in[v + off(t)][ci] W[t][co][ci] (M = voxels,
-// N = output channels, K = 27 * input channels); the kernels run it on the
-// tensor cores with mma.sync m16n8k16 (BF16 in, FP32 accumulate), operands
-// staged in shared memory and fed with ldmatrix:
-//   conv_fwd    forward, and the data gradient of the backward pass (the same
-//               GEMM with the taps mirrored and the channel roles swapped),
-//               with bias + ReLU, or the ReLU-derivative mask, in the epilogue;
-//   conv_wgrad  weight gradient, per tap a GEMM over voxels (M = Cout,
-//               N = Cin, K = voxels), split over voxel chunks whose partial
-//               sums are added in a fixed order;
+// N = output channels, K = 27 * input channels).  The forward pass and the
+// data gradient of the backward pass (the same GEMM with the taps mirrored and
+// the channel roles swapped, ReLU-derivative mask in the epilogue) run on the
+// tcgen05 tensor cores (kgs_conv_tc.cu).  This file holds
+//   conv_wgrad  the weight gradient, per tap a GEMM over voxels (M = Cout,
+//               N = Cin, K = voxels) on mma.sync m16n8k16 (bf16 in, FP32
+//               accumulate, operands fed with ldmatrix), split over voxel
+//               chunks whose partial sums are added in a fixed order;
 // plus bias gradients, the masked mean-squared-error loss, Adam, and the
 // feature / target / prediction maps between the solver's FP64 fields and the
 // network's normalised channels.

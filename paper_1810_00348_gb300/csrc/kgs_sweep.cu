@@ -6,8 +6,12 @@
 // depends only on its three upwind neighbour blocks, so the blocks are swept
 // in diagonal stages (block coordinates reflected so that the sweep runs
 // towards +x, +y, +z): stage s holds every block whose reflected coordinates
-// sum to s, for all eight octants at once.  One launch per stage; one CTA per
-// (octant, block, group of vg_size velocities of that octant).  Velocities
+// sum to s, for all eight octants at once.  A work item is (octant, block,
+// group of vg_size velocities of that octant).  The persistent kernel claims
+// items in stage order and waits (bounded) for the completion flags of the
+// item's three upwind blocks, so one launch covers the whole sweep; the
+// kernel with one launch per stage serves the entry point that allocates no
+// device memory (no flags needed).  Velocities
 // are independent within an outer iteration (Eq. (6) lags f^S, tau and
 // rho_w), which is what lets all octants and all velocity groups run
 // concurrently.
@@ -19,9 +23,9 @@
 // it is overwritten), with a halo row and column holding the values that
 // enter the slice from the upwind neighbour blocks or the domain boundary.
 // Within a slice a thread visits the cells by anti-diagonals i + j = d: the
-// cells of one diagonal are independent, so the fully unrolled diagonal loop
-// keeps up to eight update chains in flight, with the latest value of each
-// row held in registers.  Each update is the pointwise solution of Eq. (7):
+// cells of one diagonal are independent and their upwind values (i-1, j),
+// (i, j-1) were written on the previous diagonal.  Each update is the
+// pointwise solution of Eq. (7):
 //     f = (f^S/tau + sum_d a_d f_up,d) / (1/tau + sum_d a_d),  a_d = |xi_d|/dx_d,
 // with the Shakhov equilibrium f^S of Eq. (2) computed on the fly from the
 // lagged coefficients of the cell.
@@ -36,8 +40,8 @@
 // corrections): their rounding would otherwise repeat identically on every
 // line and add up coherently in the heat flux.  The line folds go into
 // Kahan-compensated sums; the per-(group, cell) partial is written to global
-// memory in FP64 and a fixed-order reduction closes the iteration (no
-// atomics).  Block faces between stages go through three face planes in
+// memory (FP64, or an FP32 Kahan pair) and a fixed-order reduction closes the
+// iteration (no atomics).  Block faces between stages go through three face planes in
 // global memory indexed by the cell position on the face: a block reads the
 // plane entries written by its upwind neighbour in the previous stage before
 // overwriting them with its own outflow.
