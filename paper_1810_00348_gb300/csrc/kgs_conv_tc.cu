@@ -21,6 +21,15 @@
 // TMEM lanes 32w..32w+31 = output rows) and applies bias + ReLU, bias only,
 // or the ReLU mask of the backward pass.
 //
+// The weight gradient (wgrad_tc_kernel) is the per-tap GEMM dW[t][co][ci] =
+// sum over voxels v of dy[v][co] in[v + off(t)][ci] with the voxels as the
+// reduction dimension.  Both tensors store voxels outermost, so a CTA loads
+// 8 x 16-voxel tiles with plain loads, transposes 8 x 8 bf16 blocks in
+// registers and writes them K-major (16-byte rows of 8 voxels of one
+// channel); output channels fill the 128 accumulator lanes (rows past Cout
+// are ignored).  A CTA accumulates a chunk of tiles of one sample for all 27
+// taps and writes its partial; the caller sums the partials in a fixed order.
+//
 // Every wait on a barrier is bounded; on expiry the CTA records the error,
 // waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include <cstdint>
@@ -304,6 +313,152 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient: part[b][chunk][t][co][ci] = sum over the chunk's voxels v
+// of dy[v][co] * in[v + off(t)][ci], one tcgen05 GEMM per (tap, chunk): M = co
+// (128 TMEM lanes, rows >= cout_p ignored), N = ci, K = voxels in steps of 16.
+// Both operands have the voxel (reduction) index outermost in memory, so a
+// tile of 128 voxels (the forward pass's 8 x 16 patch) is transposed on the
+// way into shared memory: a thread loads an 8-voxel x 8-channel block as eight
+// 16-byte rows and writes it back as eight 16-byte rows of 8 voxels of one
+// channel -- the K-major core-matrix rows.  Two tile buffers alternate: the
+// threads fill one while the tensor core works on the other.
+constexpr int WG_TILES = 32;  // voxel tiles of 128 per CTA
+
+// 8 x 8 transpose of bf16: r[j] holds channels 0..7 of voxel j (4 words of
+// two channels); o[c] receives voxels 0..7 of channel c.
+__device__ __forceinline__ void transpose8x8(const uint4 (&r)[8], uint4 (&o)[8])
+{
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(r);  // w[j * 4 + c / 2]
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const uint32_t sel = (c & 1) ? 0x7632u : 0x5410u;
+        uint32_t q[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) q[k] = __byte_perm(w[(2 * k) * 4 + c / 2], w[(2 * k + 1) * 4 + c / 2], sel);
+        o[c] = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    wgrad_tc_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ dy,
+                    float *__restrict__ part, ConvDims dm, int n_chunks, int *err)
+{
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ __align__(8) uint64_t bar[2], done_bar;
+    __shared__ uint32_t tmem_base;
+    const int cout_p = dm.cout_p, cin_p = dm.cin_p, C8o = cout_p / 8, C8i = cin_p / 8;
+    const uint32_t a_bytes = 16 * 128 * 16;               // [16 voxel octets][128 rows][8 voxels]
+    const uint32_t b_bytes = 16 * (uint32_t)cin_p * 16;   // [16 voxel octets][cin_p rows][8 voxels]
+    const uint32_t buf_bytes = a_bytes + b_bytes;
+    const uint32_t base = smem_u32(sm);
+    const int t = blockIdx.x, chunk = blockIdx.y, b = blockIdx.z;
+    const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
+    const int tiles_x = (dm.W + TX - 1) / TX, tiles_y = (dm.H + TY - 1) / TY;
+    const int n_tiles = tiles_x * tiles_y * dm.D;
+    const int tile0 = chunk * WG_TILES, tile1 = min(n_tiles, tile0 + WG_TILES);
+    const size_t vol = (size_t)dm.D * dm.H * dm.W;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar[0]), 1);
+        mbar_init(smem_u32(&bar[1]), 1);
+        mbar_init(smem_u32(&done_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // rows of A beyond cout_p feed only accumulator rows that are never read
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = instr_desc(128, cin_p);
+    bool ok = true;
+
+    for (int tile = tile0; tile < tile1; tile++) {
+        const int i = tile - tile0, q = i & 1;
+        const int tz = tile / (tiles_x * tiles_y), txy = tile % (tiles_x * tiles_y);
+        const int x0 = (txy % tiles_x) * TX, y0 = (txy / tiles_x) * TY;
+        // buffer q was read by the MMAs of tile i-2
+        if (i >= 2 && ok && !mbar_wait(smem_u32(&bar[q]), ((i - 2) >> 1) & 1)) ok = false;
+        const uint32_t abuf = base + q * buf_bytes, bbuf = abuf + a_bytes;
+        // blocks (voxel octet = patch row y, channel octet): A from dy, B from the shifted input
+        for (int blk = threadIdx.x; blk < 16 * (C8o + C8i); blk += THREADS) {
+            const bool isA = blk < 16 * C8o;
+            const int k = isA ? blk : blk - 16 * C8o;
+            const int vo = k % 16, c8 = k / 16;
+            const int gy = y0 + vo;
+            uint4 r[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int gx = x0 + j;
+                r[j] = make_uint4(0, 0, 0, 0);
+                if (gx < dm.W && gy < dm.H) {  // a voxel of the patch
+                    if (isA) {
+                        r[j] = *reinterpret_cast<const uint4 *>(
+                            dy + ((size_t)b * vol + ((size_t)tz * dm.H + gy) * dm.W + gx) * cout_p + c8 * 8);
+                    } else {
+                        const int sx = gx + kx - 1, sy = gy + ky - 1, sz = tz + kz - 1;
+                        if (sx >= 0 && sy >= 0 && sz >= 0 && sx < dm.W && sy < dm.H && sz < dm.D)
+                            r[j] = *reinterpret_cast<const uint4 *>(
+                                in + ((size_t)b * vol + ((size_t)sz * dm.H + sy) * dm.W + sx) * cin_p + c8 * 8);
+                    }
+                }
+            }
+            uint4 o[8];
+            transpose8x8(r, o);
+            const int rows = isA ? 128 : cin_p;
+            unsigned char *dst = sm + (isA ? abuf : bbuf) - base;
+#pragma unroll
+            for (int c = 0; c < 8; c++)
+                *reinterpret_cast<uint4 *>(dst + ((size_t)vo * rows + c8 * 8 + c) * 16) = o[c];
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x == 0 && ok) {
+#pragma unroll
+            for (int ks = 0; ks < 8; ks++) {  // K = 16 voxels = octets 2ks, 2ks+1
+                const uint64_t a = smem_desc(abuf + (uint32_t)(2 * ks) * 128 * 16, 128 * 16, 128);
+                const uint64_t bd = smem_desc(bbuf + (uint32_t)(2 * ks * cin_p) * 16, (uint32_t)cin_p * 16, 128);
+                tc_mma(tmem, a, bd, idesc, (i | ks) != 0);
+            }
+            tc_commit(smem_u32(&bar[q]));
+        }
+    }
+    if (threadIdx.x == 0) tc_commit(smem_u32(&done_bar));
+    const bool done = mbar_wait(smem_u32(&done_bar), 0);
+    tc_fence_after();
+    __syncthreads();
+    if (!done || !ok) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else {
+        // row co = TMEM lane; columns ci
+        const int co = warp * 32 + lane;
+        float *dst = part + (((size_t)b * n_chunks + chunk) * 27 + t) * cout_p * cin_p;
+        for (int c0 = 0; c0 < cin_p; c0 += 16) {
+            float v[16];
+            tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (co >= cout_p) continue;
+#pragma unroll
+            for (int k = 0; k < 16; k += 4)
+                *reinterpret_cast<float4 *>(dst + (size_t)co * cin_p + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
 template <int MODE>
 cudaError_t launch(const __nv_bfloat16 *in, const __nv_bfloat16 *wpk, const float *bias, void *out,
                    const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
@@ -333,6 +488,25 @@ cudaError_t conv_tc(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, _
     case 1: return launch<1>(in, wpk, bias, out, gate, dm, err, s);
     default: return launch<2>(in, wpk, bias, out, gate, dm, err, s);
     }
+}
+
+int wgrad_chunks(const ConvDims &dm)
+{
+    const int tiles = ((dm.W + TX - 1) / TX) * ((dm.H + TY - 1) / TY) * dm.D;
+    return (tiles + WG_TILES - 1) / WG_TILES;
+}
+
+cudaError_t wgrad_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *dy, float *part, ConvDims dm, int *err,
+                     cudaStream_t s)
+{
+    if (dm.cin_p % 16 || dm.cout_p % 16 || dm.cin_p < 16 || dm.cout_p < 16 || dm.cin_p > 112 || dm.cout_p > 112)
+        return cudaErrorInvalidValue;
+    const size_t smem = 2 * ((size_t)16 * 128 * 16 + (size_t)16 * dm.cin_p * 16);
+    cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int n_chunks = wgrad_chunks(dm);
+    wgrad_tc_kernel<<<dim3(27, n_chunks, dm.B), THREADS, smem, s>>>(in, dy, part, dm, n_chunks, err);
+    return cudaGetLastError();
 }
 
 }  // namespace nn

@@ -10,10 +10,9 @@
 // data gradient of the backward pass (the same GEMM with the taps mirrored and
 // the channel roles swapped, ReLU-derivative mask in the epilogue) run on the
 // tcgen05 tensor cores (kgs_conv_tc.cu).  This file holds
-//   conv_wgrad  the weight gradient, per tap a GEMM over voxels (M = Cout,
-//               N = Cin, K = voxels) on mma.sync m16n8k16 (bf16 in, FP32
-//               accumulate, operands fed with ldmatrix), split over voxel
-//               chunks whose partial sums are added in a fixed order;
+// the weight gradient (per tap a GEMM over voxels, M = Cout, N = Cin, K =
+// voxels) also runs there, split over voxel chunks; this file adds its
+// fixed-order reduction over chunks,
 // plus bias gradients, the masked mean-squared-error loss, Adam, and the
 // feature / target / prediction maps between the solver's FP64 fields and the
 // network's normalised channels.
@@ -31,145 +30,9 @@
 
 namespace {
 
-constexpr int TILE = 4;                 // spatial tile edge: 4^3 = 64 voxels per CTA
-constexpr int TV_ = TILE * TILE * TILE; // voxels per tile
-constexpr int HALO = TILE + 2;          // tile with the 1-voxel halo
-constexpr int HV = HALO * HALO * HALO;  // 216 halo voxels
-constexpr int CONV_THREADS = 128;       // 4 warps x 16 voxels
-constexpr int WG_CHUNK_TILES = 32;      // voxel tiles per weight-gradient CTA
-constexpr int WG_TILES_PER_WARP = 25;   // ceil((112/16) * (112/8) / 4) output tiles
-
-__host__ __device__ inline int pad16(int c) { return (c + 15) / 16 * 16; }
-
-__device__ __forceinline__ unsigned smem_addr(const void *p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                         unsigned b0, unsigned b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 using kgs::nn::ConvDims;
 
-// ---------------------------------------------------------------------------
-// Weight gradient: part[chunk][t][co][ci] = sum over the chunk's voxels v of
-// dy[v][co] * in[v + off(t)][ci].  CTA = (tap, chunk of WG_CHUNK_TILES tiles,
-// sample).  Per tile: dy tile [64 voxels][cout_p] and the input halo in shared
-// memory; A = dy^T (co x v) and B = in (v x ci) through transposing ldmatrix.
-__global__ void __launch_bounds__(CONV_THREADS) conv_wgrad_kernel(const __nv_bfloat16 *__restrict__ in,
-                                                                  const __nv_bfloat16 *__restrict__ dy,
-                                                                  float *__restrict__ part, ConvDims dm,
-                                                                  int n_chunks)
-{
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int cin_p = dm.cin_p, cout_p = dm.cout_p;
-    const int hs = cin_p + 8, ds = cout_p + 8;
-    __nv_bfloat16 *halo = reinterpret_cast<__nv_bfloat16 *>(sm);  // [HV][hs]
-    __nv_bfloat16 *dys = halo + HV * hs;                           // [64][ds]
-    const int t = blockIdx.x;
-    const int chunk = blockIdx.y, b = blockIdx.z;
-    const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
-    const int tiles_x = (dm.W + TILE - 1) / TILE, tiles_y = (dm.H + TILE - 1) / TILE,
-              tiles_z = (dm.D + TILE - 1) / TILE;
-    const int n_tiles = tiles_x * tiles_y * tiles_z;
-    const size_t vol = (size_t)dm.D * dm.H * dm.W;
-    const int cch = cin_p / 8, dch = cout_p / 8;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    // output tiles (m16 x n8) of the Cout x Cin block, spread over the warps
-    const int mt = cout_p / 16, nt = cin_p / 8;
-    const int n_out = mt * nt;
-    float acc[WG_TILES_PER_WARP][4];
-#pragma unroll
-    for (int j = 0; j < WG_TILES_PER_WARP; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-
-    for (int it = 0; it < WG_CHUNK_TILES; it++) {
-        const int tile = chunk * WG_CHUNK_TILES + it;
-        if (tile >= n_tiles) break;
-        const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, tz = tile / (tiles_x * tiles_y);
-        __syncthreads();  // previous tile's operands are consumed
-        // input halo
-        for (int i = threadIdx.x; i < HV * cch; i += CONV_THREADS) {
-            const int hv = i / cch, ch = i % cch;
-            const int gx = tx * TILE - 1 + hv % HALO, gy = ty * TILE - 1 + (hv / HALO) % HALO,
-                      gz = tz * TILE - 1 + hv / (HALO * HALO);
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (gx >= 0 && gy >= 0 && gz >= 0 && gx < dm.W && gy < dm.H && gz < dm.D)
-                val = *reinterpret_cast<const uint4 *>(in + ((size_t)b * vol + ((size_t)gz * dm.H + gy) * dm.W + gx) *
-                                                                 cin_p + ch * 8);
-            *reinterpret_cast<uint4 *>(halo + hv * hs + ch * 8) = val;
-        }
-        // dy tile (zero outside the volume)
-        for (int i = threadIdx.x; i < TV_ * dch; i += CONV_THREADS) {
-            const int mm = i / dch, ch = i % dch;
-            const int gx = tx * TILE + mm % TILE, gy = ty * TILE + (mm / TILE) % TILE, gz = tz * TILE + mm / (TILE * TILE);
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (gx < dm.W && gy < dm.H && gz < dm.D)
-                val = *reinterpret_cast<const uint4 *>(dy + ((size_t)b * vol + ((size_t)gz * dm.H + gy) * dm.W + gx) *
-                                                                cout_p + ch * 8);
-            *reinterpret_cast<uint4 *>(dys + mm * ds + ch * 8) = val;
-        }
-        __syncthreads();
-        // K = 64 voxels of the tile, 16 at a time
-        for (int k0 = 0; k0 < TV_; k0 += 16) {
-            // A (co x v) row-major from dys[v][co], transposed by ldmatrix:
-            // matrices (co 0-7 | 8-15) x (v 0-7 | 8-15)
-            const int av = k0 + (lane & 7) + (lane >> 4) * 8;
-            const int aco = ((lane >> 3) & 1) * 8;
-            // B (v x ci) from halo[v + off(t)][ci], transposed: v 0-7 | 8-15
-            const int bv = k0 + (lane & 7) + ((lane >> 3) & 1) * 8;
-            const int blx = bv % TILE, bly = (bv / TILE) % TILE, blz = bv / (TILE * TILE);
-            const int bhv = ((blz + kz) * HALO + (bly + ky)) * HALO + (blx + kx);
-#pragma unroll
-            for (int j = 0; j < WG_TILES_PER_WARP; j++) {
-                const int o = warp + 4 * j;
-                if (o < n_out) {
-                    const int mi = o / nt, ni = o % nt;
-                    unsigned a0, a1, a2, a3, b0, b1, b2, b3;
-                    ldsm_x4_t(smem_addr(dys + av * ds + mi * 16 + aco), a0, a1, a2, a3);
-                    ldsm_x4_t(smem_addr(halo + bhv * hs + ni * 8), b0, b1, b2, b3);
-                    (void)b2;
-                    (void)b3;
-                    mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
-                }
-            }
-        }
-    }
-    // write the chunk's partial: part[((b*n_chunks + chunk) * 27 + t)][co][ci]
-    float *dst = part + (((size_t)b * n_chunks + chunk) * 27 + t) * cout_p * cin_p;
-    const int g = lane >> 2, cpair = (lane & 3) * 2;
-#pragma unroll
-    for (int j = 0; j < WG_TILES_PER_WARP; j++) {
-        const int o = warp + 4 * j;
-        if (o < n_out) {
-            const int mi = o / nt, ni = o % nt;
-#pragma unroll
-            for (int half = 0; half < 2; half++) {
-                const int co = mi * 16 + g + half * 8, ci = ni * 8 + cpair;
-                *reinterpret_cast<float2 *>(dst + co * cin_p + ci) = make_float2(acc[j][half * 2], acc[j][half * 2 + 1]);
-            }
-        }
-    }
-}
+__host__ __device__ inline int pad16(int c) { return (c + 15) / 16 * 16; }
 
 // gW[t][co][ci] = sum over (sample, chunk) in order of the partials.
 __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int n_parts, size_t per, float *__restrict__ gw)
@@ -364,7 +227,6 @@ __global__ void apply_kernel(size_t ncell, const double *__restrict__ up, const 
 
 inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-size_t wgrad_smem(int cin_p, int cout_p) { return (size_t)HV * (cin_p + 8) * 2 + (size_t)TV_ * (cout_p + 8) * 2; }
 
 cudaError_t run_conv(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, __nv_bfloat16 *wpk,
                      const float *bias, void *out, const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s)
@@ -488,8 +350,7 @@ int backward(kgs_net *n)
 {
     cudaStream_t s = n->stream;
     const size_t nvox = (size_t)n->B * n->D * n->H * n->W;
-    const int tiles = ((n->W + TILE - 1) / TILE) * ((n->H + TILE - 1) / TILE) * ((n->D + TILE - 1) / TILE);
-    const int n_chunks = (tiles + WG_CHUNK_TILES - 1) / WG_CHUNK_TILES;
+    const int n_chunks = kgs::nn::wgrad_chunks(dims(n, 0));
     __nv_bfloat16 *gcur = n->ga, *gnext = n->gb2;
     for (int l = n->L - 1; l >= 0; l--) {
         const ConvDims dm = dims(n, l);
@@ -502,10 +363,7 @@ int backward(kgs_net *n)
             NN_CHECK(cudaMalloc(&n->wpart, need * sizeof(float)));
             n->wpart_cap = need;
         }
-        const size_t smem = wgrad_smem(dm.cin_p, dm.cout_p);
-        NN_CHECK(cudaFuncSetAttribute(conv_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        conv_wgrad_kernel<<<dim3(27, n_chunks, n->B), CONV_THREADS, smem, s>>>(n->act[l], gcur, n->wpart, dm, n_chunks);
-        NN_CHECK(cudaGetLastError());
+        NN_CHECK(kgs::nn::wgrad_tc(n->act[l], gcur, n->wpart, dm, n->d_err, s));
         wgrad_reduce_kernel<<<nblk(per, 256), 256, 0, s>>>(n->wpart, n->B * n_chunks, per, n->g + n->w_off[l]);
         NN_CHECK(cudaGetLastError());
         bias_grad_kernel<__nv_bfloat16><<<dm.cout_p, 256, 0, s>>>(gcur, nvox, dm.cout_p, n->g + n->b_off[l]);

@@ -22,5 +22,13 @@ struct ConvDims {
 cudaError_t conv_tc(int mode, const __nv_bfloat16 *in, const __nv_bfloat16 *w, __nv_bfloat16 *wpk, const float *bias,
                     void *out, const __nv_bfloat16 *gate, ConvDims dm, int *err, cudaStream_t s);
 
+// Weight gradient of the same convolution on the tensor cores:
+// part[b][chunk][t][co][ci] (FP32, wgrad_chunks(dm) chunks of voxels per
+// sample) = sum over the chunk's voxels v of dy[v][co] in[v + off(t)][ci];
+// the caller sums the partials over samples and chunks in a fixed order.
+int wgrad_chunks(const ConvDims &dm);
+cudaError_t wgrad_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *dy, float *part, ConvDims dm, int *err,
+                     cudaStream_t s);
+
 }  // namespace nn
 }  // namespace kgs
