@@ -271,7 +271,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     // persistent grid: as many CTAs as fit on the device at once
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess) return fail(KGS_ECUDA);
-    const size_t smem = sweep_smem_bytes(b->precision, b->tv, b->nxo_max);
+    const size_t smem = sweep_smem_bytes(b->precision, b->tv, b->line16, b->nxo_max);
     per_sm = sweep_persistent_occupancy(b->precision, b->tv, b->line16, b->uniform, smem);
     if (per_sm < 1) return fail(KGS_ECUDA);
     b->grid = sms * per_sm;

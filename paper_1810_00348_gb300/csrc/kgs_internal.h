@@ -136,7 +136,7 @@ int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, s
 
 // Sweep launch (one wavefront stage).  precision: 0 FP64, 1 FP32.
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s);
-size_t sweep_smem_bytes(int precision, int tv, int nxo_max);
+size_t sweep_smem_bytes(int precision, int tv, int line16, int nxo_max);
 
 struct CloseArgs {
     int nx, ny, nz;

@@ -245,7 +245,7 @@ int kgs::ctx_persist_init(kgs_ctx *c)
     KGS_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
     const SweepArgs a = ctx_sweep_args(c);
     const int per_sm = sweep_persistent_occupancy(t.precision, t.tv, a.line16, a.uniform,
-                                                  sweep_smem_bytes(t.precision, t.tv, t.nxo_max));
+                                                  sweep_smem_bytes(t.precision, t.tv, a.line16, t.nxo_max));
     if (per_sm < 1) return KGS_OK;  // keep the launch per stage
     std::vector<int4> items;
     for (int s = 0; s < (int)t.stage_n.size(); s++) ctx_stage_items(t, 0, s, items);

@@ -136,9 +136,10 @@ struct SmemLayout {
     static constexpr size_t red_bytes = sizeof(double) * NPART * SLICE;
     static constexpr size_t fixed = slice_bytes + coef_bytes + vt_bytes + red_bytes;
     static int cx_stride(int nxm) { return nxm | 1; }  // odd: conflict-free per-cell reads
-    static size_t total(int nxm)
+    // line: x-lines of LINE nodes keep their c_x in registers (no c_x tables)
+    static size_t total(int nxm, bool line)
     {
-        return fixed + align16(sizeof(Real) * 2 * nxm) + 2 * align16(sizeof(Real) * SLICE * cx_stride(nxm));
+        return fixed + align16(sizeof(Real) * 2 * nxm) + (line ? 0 : 2 * align16(sizeof(Real) * SLICE * cx_stride(nxm)));
     }
 };
 
@@ -767,7 +768,7 @@ cudaError_t launch_t(const SweepArgs &a, int n_items, int max_vg, cudaStream_t s
 {
     using L = SmemLayout<Real, TV>;
     static size_t configured = 0;
-    const size_t bytes = L::total(a.nxo_max);
+    const size_t bytes = L::total(a.nxo_max, LINE > 0);
     if (bytes > configured) {
         cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Real, TV, LINE, UNIF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -794,7 +795,7 @@ cudaError_t launch_persistent_t(const BatchSweepArgs &b, int nxo_max, int grid, 
 {
     using L = SmemLayout<Real, TV>;
     static size_t configured = 0;
-    const size_t bytes = L::total(nxo_max);
+    const size_t bytes = L::total(nxo_max, LINE > 0);
     if (bytes > configured) {
         cudaError_t e = cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE, UNIF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -866,10 +867,11 @@ cudaError_t launch_sweep_persistent(int precision, int tv, int line16, int unifo
     return dispatch<PersistentLaunch>(precision, tv, line16, uniform, b, nxo_max, grid, s);
 }
 
-size_t sweep_smem_bytes(int precision, int tv, int nxo_max)
+size_t sweep_smem_bytes(int precision, int tv, int line16, int nxo_max)
 {
-    if (precision == 0) return SmemLayout<double, 1>::total(nxo_max);
-    return tv == 2 ? SmemLayout<float, 2>::total(nxo_max) : SmemLayout<float, 1>::total(nxo_max);
+    const bool line = line16 != 0;
+    if (precision == 0) return SmemLayout<double, 1>::total(nxo_max, line);
+    return tv == 2 ? SmemLayout<float, 2>::total(nxo_max, line) : SmemLayout<float, 1>::total(nxo_max, line);
 }
 
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s)

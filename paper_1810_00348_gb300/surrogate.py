@@ -250,6 +250,8 @@ def main(argv=None):
     ap.add_argument("--eval-kn", default="0.5", help="Knudsen numbers of the extra evaluation")
     ap.add_argument("--forward-only", type=int, default=0,
                     help="only time forward passes of the untrained network on one N^3 volume and exit")
+    ap.add_argument("--train-only", type=int, default=0,
+                    help="only time training steps of the network on a batch of 4 random N^3 volumes and exit")
     args = ap.parse_args(argv)
     kgs.load()
     if args.forward_only:
@@ -265,6 +267,20 @@ def main(argv=None):
             kgs.kgs_net_forward(s.net, x.data_ptr(), shape, y.data_ptr())
             ms.append((time.perf_counter() - t1) * 1e3)
         print(json.dumps({"forward_ms": ms[1:], "voxels": n ** 3}))
+        return
+    if args.train_only:
+        n = args.train_only
+        s = Surrogate(seed=0)
+        shape = (4, n, n, n)
+        x = torch.randn(shape + (N_FEATURES,), device="cuda")
+        t = torch.randn(shape + (N_FIELDS,), device="cuda")
+        ms = []
+        for _ in range(4):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            kgs.kgs_net_train_step(s.net, x.data_ptr(), t.data_ptr(), None, shape, 1e-5)
+            ms.append((time.perf_counter() - t1) * 1e3)
+        print(json.dumps({"train_step_ms": ms[1:], "voxels": 4 * n ** 3}))
         return
     t0 = time.perf_counter()
     samples = make_samples(draw_cavities(args.samples, seed=1, cells=args.cells, vels=args.vels),
