@@ -43,16 +43,26 @@ __global__ void coef_kernel(const double *__restrict__ mac, const uint8_t *__res
         const double rtau = p / (mu_ref * pow(T, omega));
         const double A = rho / pow(2.0 * M_PI * RT, 1.5);
         const double sh = (1.0 - Pr) / (5.0 * p * RT);
-        out[C_UX] = (Real)mac[1 * ncell + c];
-        out[C_UY] = (Real)mac[2 * ncell + c];
-        out[C_UZ] = (Real)mac[3 * ncell + c];
-        // the FP32 sweep takes kappa as log2(kappa) inside its exponent
-        out[C_KAPPA] = sizeof(Real) == 8 ? (Real)(rtau * A) : (Real)log2(rtau * A);
+        // centre U^n in the sweep precision, stored doubled and negated (exact)
+        const double U[3] = {(double)(Real)mac[1 * ncell + c], (double)(Real)mac[2 * ncell + c],
+                             (double)(Real)mac[3 * ncell + c]};
+        const double q[3] = {(double)(Real)(sh * mac[5 * ncell + c]), (double)(Real)(sh * mac[6 * ncell + c]),
+                             (double)(Real)(sh * mac[7 * ncell + c])};
+        const double U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+        out[C_M2UX] = (Real)(-2.0 * U[0]);
+        out[C_M2UY] = (Real)(-2.0 * U[1]);
+        out[C_M2UZ] = (Real)(-2.0 * U[2]);
+        // exp(-|c|^2/(2RT)) = exp(-|U|^2/(2RT)) exp(-(|xi|^2 + s)/(2RT)); the FP32
+        // sweep takes kappa as a base-2 logarithm inside its exponent
+        out[C_KAPPA] = sizeof(Real) == 8 ? (Real)(rtau * A * exp(-U2 / (2.0 * RT)))
+                                         : (Real)(log2(rtau * A) - LOG2E * U2 / (2.0 * RT));
         out[C_NEXP] = sizeof(Real) == 8 ? (Real)(-1.0 / (2.0 * RT)) : (Real)(-LOG2E / (2.0 * RT));
         out[C_RT1] = (Real)(1.0 / RT);
-        out[C_QX] = (Real)(sh * mac[5 * ncell + c]);
-        out[C_QY] = (Real)(sh * mac[6 * ncell + c]);
-        out[C_QZ] = (Real)(sh * mac[7 * ncell + c]);
+        out[C_QX] = (Real)q[0];
+        out[C_QY] = (Real)q[1];
+        out[C_QZ] = (Real)q[2];
+        out[C_SHK0] = (Real)(U2 / RT - 5.0);
+        out[C_MUQ] = (Real)(-(U[0] * q[0] + U[1] * q[1] + U[2] * q[2]));
         out[C_RTAU] = (Real)rtau;
         out[C_RDX] = (Real)rdx[i];
         out[C_RDY] = (Real)rdy[j];
@@ -161,7 +171,7 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
         const Real *cf = static_cast<const Real *>(a.coef) + c * NCOEF;
         // The sums were taken about the lagged velocity U^n as stored in the
         // sweep precision; shift exactly to U^{n+1} = U^n + delta.
-        const double Uc[3] = {(double)cf[C_UX], (double)cf[C_UY], (double)cf[C_UZ]};
+        const double Uc[3] = {-0.5 * (double)cf[C_M2UX], -0.5 * (double)cf[C_M2UY], -0.5 * (double)cf[C_M2UZ]};
         const double rho = S[P_S0];
         const double d[3] = {S[P_S1X] / rho, S[P_S1Y] / rho, S[P_S1Z] / rho};
         const double S2[3][3] = {{S[P_S2XX], S[P_S2XY], S[P_S2XZ]},

@@ -19,17 +19,21 @@ constexpr int NCOEF = 16;        // per-cell coefficient record
 constexpr int NPART = 16;        // per-cell partial: 13 moment sums + 3 wall fluxes
 
 // Per-cell coefficient record (computed from the lagged FP64 macros each
-// iteration, stored in the sweep precision).
+// iteration, stored in the sweep precision).  U^n below is the lagged velocity
+// as rounded to the sweep precision: the centre of c = xi - U^n for the
+// moments.  The equilibrium is evaluated from s = |xi|^2 - 2 U^n . xi, which
+// is |c|^2 - |U^n|^2; the |U^n|^2 terms are folded into the constants below.
 enum {
-    C_UX = 0, C_UY, C_UZ,   // lagged velocity U^n: centre of c = xi - U^n
-    C_KAPPA,                // (1/tau) rho (2 pi R T)^{-3/2}; FP32 path: its base-2 logarithm
+    C_M2UX = 0, C_M2UY, C_M2UZ,  // -2 U^n (exactly twice the centre, negated)
+    C_KAPPA,                // (1/tau) rho (2 pi R T)^{-3/2} exp(-|U^n|^2 / (2RT)); FP32: its base-2 logarithm
     C_NEXP,                 // exponent scale: -1/(2RT) (FP64) or -log2(e)/(2RT) (FP32)
     C_RT1,                  // 1/(R T)
     C_RTAU,                 // 1/tau
     C_FLAGS,                // cell flags (below), their bits stored in the value (flag_value)
-    C_QX, C_QY, C_QZ,       // (1 - Pr) q / (5 p R T)
+    C_QX, C_QY, C_QZ,       // q' = (1 - Pr) q / (5 p R T)
     C_RDX, C_RDY, C_RDZ,    // 1/dx_i, 1/dy_j, 1/dz_k
-    C_PAD0, C_PAD1
+    C_SHK0,                 // |U^n|^2 / (R T) - 5, so that |c|^2/(RT) - 5 = s/(RT) + C_SHK0
+    C_MUQ                   // -U^n . q'
 };
 
 // Cell flags.

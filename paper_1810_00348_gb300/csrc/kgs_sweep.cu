@@ -276,6 +276,13 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         mgz[m] = mt[(size_t)rowz * Nv + gv[m]];
         msol[m] = mt[(size_t)MT_SOLID * Nv + gv[m]];
     }
+    // |xi|^2 of each velocity, rounded once from its FP64 value
+    Real xsq[TV];
+#pragma unroll
+    for (int m = 0; m < TV; m++) {
+        const double x0 = xi[m][0], x1 = xi[m][1], x2 = xi[m][2];
+        xsq[m] = Real(x0 * x0 + x1 * x1 + x2 * x2);
+    }
     // uniform grid: the upwind coefficients a_d = abs(xi_d) / dx_d and their
     // sum depend on the velocity only
     Real adx[TV][3], asum[TV];
@@ -417,7 +424,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         // (lines of LINE nodes keep theirs in registers instead)
         if constexpr (LINE == 0) {
             const int cl = t % SLICE, vp = t / SLICE;
-            const Real ux = cs[cl * NCOEF + C_UX];
+            const Real ux = Real(-0.5) * cs[cl * NCOEF + C_M2UX];
             for (int ix = vp; ix < nxo; ix += NT / SLICE) {
                 Real s, e;
                 two_diff(xn[ix * 2], ux, s, e);
@@ -442,11 +449,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                     const Real *c = cs + (lj * BX + li) * NCOEF;
                     const Quad<Real> c0 = load_quad(c), c1 = load_quad(c + 4), c2v = load_quad(c + 8),
                                      c3 = load_quad(c + 12);
-                    const Real ux = c0.x, uy = c0.y, uz = c0.z, kappa = c0.w;
+                    const Real m2ux = c0.x, m2uy = c0.y, m2uz = c0.z, kappa = c0.w;
                     const Real nexp = c1.x, rt1 = c1.y, rtau = c1.z;
                     const int flags = flag_bits(c1.w);
                     const Real qx = c2v.x, qy = c2v.y, qz = c2v.z, rdx = c2v.w;
-                    const Real rdy = c3.x, rdz = c3.y;
+                    const Real rdy = c3.x, rdz = c3.y, shk0 = c3.z, muq = c3.w;
                     if (!(flags & F_SOLID)) {
                         bool sol_x = false, sol_y = false, sol_z = false;
                         Real rwx = 0, rwy = 0, rwz = 0;
@@ -471,14 +478,15 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                                 if (sol_y) fy = rwy * msol[m];
                                 if (sol_z) fz = rwz * msol[m];
                             }
-                            const Real cx = xi[m][0] - ux, cy = xi[m][1] - uy, cz = xi[m][2] - uz;
-                            const Real c2 = cx * cx + cy * cy + cz * cz;
-                            const Real cq = cx * qx + cy * qy + cz * qz;
+                            // |c|^2 - |U|^2 = |xi|^2 - 2 U.xi and c.q' = xi.q' - U.q'
+                            const Real s = fma(xi[m][0], m2ux, fma(xi[m][1], m2uy, fma(xi[m][2], m2uz, xsq[m])));
+                            const Real cq = fma(xi[m][0], qx, fma(xi[m][1], qy, fma(xi[m][2], qz, muq)));
+                            const Real shak = fma(cq, fma(s, rt1, shk0), Real(1));
                             Real src;
                             if constexpr (sizeof(Real) == 4)  // kappa enters as log2(kappa) in the exponent
-                                src = eq_exp(fma(c2, nexp, kappa)) * (Real(1) + cq * (c2 * rt1 - Real(5)));
+                                src = eq_exp(fma(s, nexp, kappa)) * shak;
                             else
-                                src = kappa * eq_exp(c2 * nexp) * (Real(1) + cq * (c2 * rt1 - Real(5)));
+                                src = kappa * eq_exp(s * nexp) * shak;
                             Real ax, ay, az, den;
                             if constexpr (UNIF) {
                                 ax = adx[m][0];
@@ -536,7 +544,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
             const int flags = flag_bits(c[C_FLAGS + 0]);
             RunSum<Real> S[NPART];
             if (valid && !(flags & F_SOLID)) {
-                const Real ux = c[C_UX], uy = c[C_UY], uz = c[C_UZ];
+                const Real ux = Real(-0.5) * c[C_M2UX], uy = Real(-0.5) * c[C_M2UY], uz = Real(-0.5) * c[C_M2UZ];
                 const bool wx = flags & (F_WALL_SIDE << headx);
                 const bool wy = flags & (F_WALL_SIDE << heady);
                 const bool wz = flags & (F_WALL_SIDE << headz);
