@@ -32,6 +32,7 @@
 //
 // Every wait on a barrier is bounded; on expiry the CTA records the error,
 // waits (bounded) for its own MMAs, frees its tensor memory and returns.
+#include <algorithm>
 #include <cstdint>
 
 #include "kgs_nn.h"
@@ -315,29 +316,48 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // ---------------------------------------------------------------------------
 // Weight gradient: part[b][chunk][t][co][ci] = sum over the chunk's voxels v
-// of dy[v][co] * in[v + off(t)][ci], one tcgen05 GEMM per (tap, chunk): M = co
-// (128 TMEM lanes, rows >= cout_p ignored), N = ci, K = voxels in steps of 16.
-// Both operands have the voxel (reduction) index outermost in memory, so a
-// tile of 128 voxels (the forward pass's 8 x 16 patch) is transposed on the
-// way into shared memory: a thread loads an 8-voxel x 8-channel block as eight
-// 16-byte rows and writes it back as eight 16-byte rows of 8 voxels of one
-// channel -- the K-major core-matrix rows.  Two tile buffers alternate: the
-// threads fill one while the tensor core works on the other.
+// of dy[v][co] * in[v + off(t)][ci], per tap a tcgen05 GEMM with M = co (128
+// TMEM lanes, rows >= cout_p ignored), N = ci and K = voxels in steps of 16.
+// Both tensors store the channels of a voxel contiguously, which for this
+// GEMM is the MN-major operand layout: a core matrix is 8 voxels (along K) x
+// 8 channels (16 bytes), so tiles move with 16-byte asynchronous copies and
+// need no transpose.  A CTA takes the three taps that share (kz, ky) -- three
+// accumulators in tensor memory -- for a chunk of 8 x 16-voxel tiles.  Per
+// tile it stages dy of the tile, [y][co/8][x][16 B], and rows y0 + ky - 1 ..
+// y0 + ky + 14, columns x0 - 1 .. x0 + 8 of input plane z + kz - 1,
+// [y][ci/8][x][16 B]; the windows of that block at x offsets 0, 1, 2 are the
+// B operands of the three taps.  Three tile buffers rotate: the copies of
+// tile i + 2 are in flight while the tensor core works on tile i.
 constexpr int WG_TILES = 32;  // voxel tiles of 128 per CTA
+constexpr int WG_BUF = 3;     // tile buffers
+constexpr int WG_TMEM = 512;  // three accumulators of 128 columns
 
-// 8 x 8 transpose of bf16: r[j] holds channels 0..7 of voxel j (4 words of
-// two channels); o[c] receives voxels 0..7 of channel c.
-__device__ __forceinline__ void transpose8x8(const uint4 (&r)[8], uint4 (&o)[8])
+// kind::f16 instruction descriptor with both operands MN-major (bits 15, 16).
+__host__ __device__ constexpr uint32_t instr_desc_mn(int M, int N)
 {
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(r);  // w[j * 4 + c / 2]
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const uint32_t sel = (c & 1) ? 0x7632u : 0x5410u;
-        uint32_t q[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) q[k] = __byte_perm(w[(2 * k) * 4 + c / 2], w[(2 * k + 1) * 4 + c / 2], sel);
-        o[c] = make_uint4(q[0], q[1], q[2], q[3]);
-    }
+    return instr_desc(M, N) | (1u << 15) | (1u << 16);
+}
+
+struct WgLayout {
+    uint32_t a_bytes, h_bytes, buf_bytes, total;
+};
+// Shared memory of the weight-gradient CTA: WG_BUF x (dy tile, input block),
+// then a pad such that every MMA read stays inside the allocation even if
+// the two descriptor strides were applied the other way round.
+__host__ __device__ inline WgLayout wg_layout(int cin_p, int cout_p)
+{
+    const int c8o = cout_p / 8, c8i = cin_p / 8;
+    WgLayout L;
+    L.a_bytes = (uint32_t)(TY * c8o * TX * 16);
+    L.h_bytes = (uint32_t)(TY * c8i * HX * 16);
+    L.buf_bytes = L.a_bytes + L.h_bytes;
+    const int over_a = 13 * c8o * 128 + 256 - (int)L.h_bytes;  // past the buffer end, strides swapped
+    const int over_b = c8i * (c8i - 3) * HX * 16 + 2 * HX * 16;
+    int pad = 2048;
+    if (over_a > pad) pad = over_a;
+    if (over_b > pad) pad = over_b;
+    L.total = WG_BUF * L.buf_bytes + (uint32_t)pad + 128;
+    return L;
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -345,117 +365,123 @@ __global__ void __launch_bounds__(THREADS, 1)
                     float *__restrict__ part, ConvDims dm, int n_chunks, int *err)
 {
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ __align__(8) uint64_t bar[2], done_bar;
+    __shared__ __align__(8) uint64_t bar[WG_BUF], done_bar;
     __shared__ uint32_t tmem_base;
     const int cout_p = dm.cout_p, cin_p = dm.cin_p, C8o = cout_p / 8, C8i = cin_p / 8;
-    const uint32_t a_bytes = 16 * 128 * 16;               // [16 voxel octets][128 rows][8 voxels]
-    const uint32_t b_bytes = 16 * (uint32_t)cin_p * 16;   // [16 voxel octets][cin_p rows][8 voxels]
-    const uint32_t buf_bytes = a_bytes + b_bytes;
+    const WgLayout L = wg_layout(cin_p, cout_p);
     const uint32_t base = smem_u32(sm);
-    const int t = blockIdx.x, chunk = blockIdx.y, b = blockIdx.z;
-    const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
+    const int g = blockIdx.x, chunk = blockIdx.y, b = blockIdx.z;
+    const int kz = g / 3, ky = g % 3;  // taps 9 kz + 3 ky + kx, kx = 0, 1, 2
     const int tiles_x = (dm.W + TX - 1) / TX, tiles_y = (dm.H + TY - 1) / TY;
     const int n_tiles = tiles_x * tiles_y * dm.D;
-    const int tile0 = chunk * WG_TILES, tile1 = min(n_tiles, tile0 + WG_TILES);
+    const int tile0 = chunk * WG_TILES, nt = min(n_tiles, tile0 + WG_TILES) - tile0;
     const size_t vol = (size_t)dm.D * dm.H * dm.W;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
     if (threadIdx.x == 0) {
-        mbar_init(smem_u32(&bar[0]), 1);
-        mbar_init(smem_u32(&bar[1]), 1);
+        for (int q = 0; q < WG_BUF; q++) mbar_init(smem_u32(&bar[q]), 1);
         mbar_init(smem_u32(&done_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(TMEM_COLS)
+                     "r"(WG_TMEM)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // rows of A beyond cout_p feed only accumulator rows that are never read
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = instr_desc(128, cin_p);
-    bool ok = true;
+    const uint32_t idesc = instr_desc_mn(128, cin_p);
 
-    for (int tile = tile0; tile < tile1; tile++) {
-        const int i = tile - tile0, q = i & 1;
+    // asynchronous copies of tile tile0 + i into buffer i % WG_BUF (one group)
+    auto load_tile = [&](int i) {
+        const int tile = tile0 + i;
         const int tz = tile / (tiles_x * tiles_y), txy = tile % (tiles_x * tiles_y);
         const int x0 = (txy % tiles_x) * TX, y0 = (txy / tiles_x) * TY;
-        // buffer q was read by the MMAs of tile i-2
-        if (i >= 2 && ok && !mbar_wait(smem_u32(&bar[q]), ((i - 2) >> 1) & 1)) ok = false;
-        const uint32_t abuf = base + q * buf_bytes, bbuf = abuf + a_bytes;
-        // blocks (voxel octet = patch row y, channel octet): A from dy, B from the shifted input
-        for (int blk = threadIdx.x; blk < 16 * (C8o + C8i); blk += THREADS) {
-            const bool isA = blk < 16 * C8o;
-            const int k = isA ? blk : blk - 16 * C8o;
-            const int vo = k % 16, c8 = k / 16;
-            const int gy = y0 + vo;
-            uint4 r[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const int gx = x0 + j;
-                r[j] = make_uint4(0, 0, 0, 0);
-                if (gx < dm.W && gy < dm.H) {  // a voxel of the patch
-                    if (isA) {
-                        r[j] = *reinterpret_cast<const uint4 *>(
-                            dy + ((size_t)b * vol + ((size_t)tz * dm.H + gy) * dm.W + gx) * cout_p + c8 * 8);
-                    } else {
-                        const int sx = gx + kx - 1, sy = gy + ky - 1, sz = tz + kz - 1;
-                        if (sx >= 0 && sy >= 0 && sz >= 0 && sx < dm.W && sy < dm.H && sz < dm.D)
-                            r[j] = *reinterpret_cast<const uint4 *>(
-                                in + ((size_t)b * vol + ((size_t)sz * dm.H + sy) * dm.W + sx) * cin_p + c8 * 8);
-                    }
-                }
-            }
-            uint4 o[8];
-            transpose8x8(r, o);
-            const int rows = isA ? 128 : cin_p;
-            unsigned char *dst = sm + (isA ? abuf : bbuf) - base;
-#pragma unroll
-            for (int c = 0; c < 8; c++)
-                *reinterpret_cast<uint4 *>(dst + ((size_t)vo * rows + c8 * 8 + c) * 16) = o[c];
+        const uint32_t abuf = base + (uint32_t)(i % WG_BUF) * L.buf_bytes, hbuf = abuf + L.a_bytes;
+        for (int k = threadIdx.x; k < TX * TY * C8o; k += THREADS) {
+            const int c8 = k % C8o, v = k / C8o, vx = v % TX, vy = v / TX;
+            const int gx = x0 + vx, gy = y0 + vy;
+            const bool ok = gx < dm.W && gy < dm.H;
+            const __nv_bfloat16 *src =
+                ok ? dy + ((size_t)b * vol + ((size_t)tz * dm.H + gy) * dm.W + gx) * cout_p + c8 * 8 : dy;
+            cp_async16(abuf + (uint32_t)((vy * C8o + c8) * TX + vx) * 16, src, ok);
+        }
+        const int sz = tz + kz - 1;
+        for (int k = threadIdx.x; k < TY * HX * C8i; k += THREADS) {
+            const int c8 = k % C8i, h = k / C8i, hx = h % HX, hy = h / HX;
+            const int sx = x0 + hx - 1, sy = y0 + hy + ky - 1;
+            const bool ok = sz >= 0 && sz < dm.D && sx >= 0 && sx < dm.W && sy >= 0 && sy < dm.H;
+            const __nv_bfloat16 *src =
+                ok ? in + ((size_t)b * vol + ((size_t)sz * dm.H + sy) * dm.W + sx) * cin_p + c8 * 8 : in;
+            cp_async16(hbuf + (uint32_t)((hy * C8i + c8) * HX + hx) * 16, src, ok);
+        }
+        cp_async_commit();
+    };
+
+    bool ok = true;
+    for (int i = 0; i < WG_BUF - 1 && i < nt; i++) load_tile(i);
+    for (int i = 0; i < nt; i++) {
+        const int j = i + WG_BUF - 1;
+        if (j < nt) {
+            // tile j reuses the buffer of tile i - 1: its MMAs must have completed
+            if (i >= 1 && ok && !mbar_wait(smem_u32(&bar[(i - 1) % WG_BUF]), ((i - 1) / WG_BUF) & 1)) ok = false;
+            load_tile(j);
+            cp_async_wait<WG_BUF - 1>();  // tile i has landed
+        } else if (i + 1 < nt) {
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (threadIdx.x == 0 && ok) {
+            const uint32_t abuf = base + (uint32_t)(i % WG_BUF) * L.buf_bytes, hbuf = abuf + L.a_bytes;
+#pragma unroll 1
+            for (int ks = 0; ks < TY / 2; ks++) {  // K = 16 voxels: tile rows 2ks, 2ks + 1
+                const uint64_t a = smem_desc(abuf + (uint32_t)(2 * ks * C8o * TX) * 16, (uint32_t)(C8o * TX * 16), TX * 16);
 #pragma unroll
-            for (int ks = 0; ks < 8; ks++) {  // K = 16 voxels = octets 2ks, 2ks+1
-                const uint64_t a = smem_desc(abuf + (uint32_t)(2 * ks) * 128 * 16, 128 * 16, 128);
-                const uint64_t bd = smem_desc(bbuf + (uint32_t)(2 * ks * cin_p) * 16, (uint32_t)cin_p * 16, 128);
-                tc_mma(tmem, a, bd, idesc, (i | ks) != 0);
+                for (int kx = 0; kx < 3; kx++) {
+                    const uint64_t bd =
+                        smem_desc(hbuf + (uint32_t)(2 * ks * C8i * HX + kx) * 16, (uint32_t)(C8i * HX * 16), HX * 16);
+                    tc_mma(tmem + (uint32_t)(kx * 128), a, bd, idesc, (i | ks) != 0);
+                }
             }
-            tc_commit(smem_u32(&bar[q]));
+            tc_commit(smem_u32(&bar[i % WG_BUF]));
         }
     }
     if (threadIdx.x == 0) tc_commit(smem_u32(&done_bar));
     const bool done = mbar_wait(smem_u32(&done_bar), 0);
     tc_fence_after();
-    __syncthreads();
-    if (!done || !ok) {
+    const bool good = __syncthreads_and(done && ok) != 0;  // uniform: the loads below are warp-collective
+    if (!good) {
         if (threadIdx.x == 0) atomicExch(err, 1);
     } else {
-        // row co = TMEM lane; columns ci
+        // row co = TMEM lane; columns kx * 128 + ci
         const int co = warp * 32 + lane;
-        float *dst = part + (((size_t)b * n_chunks + chunk) * 27 + t) * cout_p * cin_p;
-        for (int c0 = 0; c0 < cin_p; c0 += 16) {
-            float v[16];
-            tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (co >= cout_p) continue;
+        for (int kx = 0; kx < 3; kx++) {
+            const int t = (kz * 3 + ky) * 3 + kx;
+            float *dst = part + (((size_t)b * n_chunks + chunk) * 27 + t) * cout_p * cin_p;
+            for (int c0 = 0; c0 < cin_p; c0 += 16) {
+                float v[16];
+                tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kx * 128 + c0), v);
+                if (co >= cout_p) continue;
 #pragma unroll
-            for (int k = 0; k < 16; k += 4)
-                *reinterpret_cast<float4 *>(dst + (size_t)co * cin_p + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                for (int k = 0; k < 16; k += 4)
+                    *reinterpret_cast<float4 *>(dst + (size_t)co * cin_p + c0 + k) =
+                        make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WG_TMEM) : "memory");
     }
 }
 
@@ -501,11 +527,12 @@ cudaError_t wgrad_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *dy, float *pa
 {
     if (dm.cin_p % 16 || dm.cout_p % 16 || dm.cin_p < 16 || dm.cout_p < 16 || dm.cin_p > 112 || dm.cout_p > 112)
         return cudaErrorInvalidValue;
-    const size_t smem = 2 * ((size_t)16 * 128 * 16 + (size_t)16 * dm.cin_p * 16);
+    // at least 120 KB: one CTA per SM, so no CTA waits for tensor memory held by another
+    const size_t smem = std::max<size_t>(wg_layout(dm.cin_p, dm.cout_p).total, 120 * 1024);
     cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int n_chunks = wgrad_chunks(dm);
-    wgrad_tc_kernel<<<dim3(27, n_chunks, dm.B), THREADS, smem, s>>>(in, dy, part, dm, n_chunks, err);
+    wgrad_tc_kernel<<<dim3(9, n_chunks, dm.B), THREADS, smem, s>>>(in, dy, part, dm, n_chunks, err);
     return cudaGetLastError();
 }
 
