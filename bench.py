@@ -40,7 +40,7 @@ FLOPS_PER_PP = 68
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch (ncu, 32^3
 # cells x 32^3 velocities, 256 velocities per CTA, blocks 8x8x32): 2.108e9 B
 # over 1.074e9 phase points
-TRAFFIC_BYTES_PER_PP = 2.108e9 / 1.074e9
+TRAFFIC_BYTES_PER_PP = 2.109e9 / 1.074e9
 TRAFFIC_SHAPE = (256, 32)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
