@@ -259,9 +259,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_commit(smem_u32(&done_bar));  // all MMAs issued by this thread
     }
-    // all MMAs of the CTA are complete once the done barrier has fired
-    const bool done = mbar_wait(smem_u32(&done_bar), 0);
-    __syncthreads();
+    // all MMAs of the CTA are complete once the done barrier has fired; the
+    // verdict is made uniform because the loads below are warp-collective
+    const bool done = __syncthreads_and(mbar_wait(smem_u32(&done_bar), 0)) != 0;
     const int last = s_last;
     const uint32_t tmem = tmem_base;
     tc_fence_after();
