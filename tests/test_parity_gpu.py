@@ -142,6 +142,34 @@ def test_mixed_one_iteration(kgs):
     assert_fields_close(kgs.kgs_moments(ctx), o.macros(), MIXED_TOL, what="mixed")
 
 
+@pytest.fixture(scope="module")
+def line16_case():
+    """32 velocity nodes per axis (octant x-lines of 16 nodes: the moment loop
+    specialised to 16-node lines, as in the benchmark) on a ragged 9 x 7 x 10
+    grid from a random state; two oracle iterations (about 1.3e7 phase points
+    each)."""
+    p = inputs.cavity([9, 7, 10], 32, L_v=4.0, lid=0.2, Kn=0.5)
+    mac = inputs.random_macros(p, 301)
+    o = Oracle(p, mac)
+    o.iterate()
+    o.iterate()
+    return p, mac, o.macros(), o.rho_w()
+
+
+@pytest.mark.parametrize("precision,vpc", [("fp64", 0), ("mixed", 128), ("mixed", 256)])
+def test_line16_against_oracle(kgs, line16_case, precision, vpc):
+    p, mac, ref, ref_rw = line16_case
+    prec = kgs.KGS_FP64 if precision == "fp64" else kgs.KGS_MIXED
+    ctx = kgs.kgs_setup(p, precision=prec, v_per_cta=vpc)
+    kgs.kgs_set_initial(ctx, mac)
+    rc, done, _ = kgs.kgs_iterate(ctx, 2)
+    assert rc == kgs.KGS_OK and done == 2
+    tol = FP64_TOL if precision == "fp64" else MIXED_TOL
+    assert_fields_close(kgs.kgs_moments(ctx), ref, tol, what="32-node lines, %s" % precision)
+    if precision == "fp64":
+        assert_rho_w_close(kgs.kgs_rho_w(ctx), ref_rw, FP64_TOL)
+
+
 def test_deterministic_and_resumable(kgs):
     p = inputs.cavity([12, 10, 14], 8, L_v=3.5, lid=0.2, Kn=0.5)
     a = kgs.kgs_setup(p, precision=kgs.KGS_MIXED)
