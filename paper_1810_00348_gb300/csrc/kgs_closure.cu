@@ -323,11 +323,18 @@ __global__ void __launch_bounds__(RED_THREADS)
     out[1] = bad ? 1.0 : 0.0;
 }
 
-// rho_w^0 from the flux of f^{S,0}: one warp per (side, cell) face; the
-// lanes split the velocities and the warp sums in a fixed order.
+// rho_w^0 from the flux of f^{S,0} through each wall face (Eq. (9) with the
+// initial state).  On the tensor-product grid the Maxwellian factorises by
+// axis and the Shakhov factor is a cubic polynomial in c, so the flux is a sum
+// of products of 1D sums S_e^a = sum_i w_i c_i^a exp(-c_i^2 / (2RT)), a = 0..3,
+// along the two tangential axes and of the half-range sums with the extra
+// factor |xi_n| (only velocities pointing into the wall) along the normal
+// axis.  One warp per (side, cell) face; the lanes split the nodes of each
+// axis and the warp sums them in a fixed order.
 __global__ void __launch_bounds__(128) wall_flux_init_kernel(const double *mac, const int8_t *wall_kind,
-                                                             const double *wall_norm, const double *vel64, int Nv,
-                                                             size_t ncell, double R, double Pr, double *rho_w)
+                                                             const double *wall_norm, const double *axis64, int nvx,
+                                                             int nvy, int nvz, size_t ncell, double R, double Pr,
+                                                             double *rho_w)
 {
     const size_t idx = (size_t)blockIdx.x * 4 + threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
@@ -346,18 +353,33 @@ __global__ void __launch_bounds__(128) wall_flux_init_kernel(const double *mac, 
     const double A = rho / pow(2.0 * M_PI * RT, 1.5);
     const int d = s / 2;
     const double nrm = (s % 2) ? -1.0 : 1.0;  // normal from the wall into the gas
-    double F = 0.0;
-    for (int g = lane; g < Nv; g += 32) {
-        const double *v = vel64 + (size_t)g * 4;
-        const double xn = v[d] * nrm;
-        if (!(xn < 0.0)) continue;
-        const double cx = v[0] - U[0], cy = v[1] - U[1], cz = v[2] - U[2];
-        const double c2 = cx * cx + cy * cy + cz * cz;
-        const double cq = cx * q[0] + cy * q[1] + cz * q[2];
-        const double fS = A * exp(-c2 / (2.0 * RT)) * (1.0 + (1.0 - Pr) * cq / (5.0 * p * RT) * (c2 / RT - 5.0));
-        F += v[3] * (-xn) * fS;
+    const int nv[3] = {nvx, nvy, nvz};
+    const int off[3] = {0, nvx, nvx + nvy};
+    const double *w = axis64 + nvx + nvy + nvz;
+    double S[3][4];
+    for (int e = 0; e < 3; e++) {
+        double m[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = lane; i < nv[e]; i += 32) {
+            const double x = axis64[off[e] + i], ce = x - U[e];
+            double g = w[off[e] + i] * exp(-ce * ce / (2.0 * RT));
+            if (e == d) g = (x * nrm < 0.0) ? g * (-x * nrm) : 0.0;
+            m[0] += g;
+            m[1] += g * ce;
+            m[2] += g * ce * ce;
+            m[3] += g * ce * ce * ce;
+        }
+        for (int a = 0; a < 4; a++) {
+            for (int o = 16; o > 0; o >>= 1) m[a] += __shfl_xor_sync(0xffffffffu, m[a], o);
+            S[e][a] = m[a];
+        }
     }
-    for (int off = 16; off > 0; off >>= 1) F += __shfl_down_sync(0xffffffffu, F, off);
+    auto P = [&](int px, int py, int pz) { return S[0][px] * S[1][py] * S[2][pz]; };
+    // sum over incoming velocities of w |xi_n| e (c.q) |c|^2 and of w |xi_n| e (c.q)
+    const double cq3 = q[0] * (P(3, 0, 0) + P(1, 2, 0) + P(1, 0, 2)) + q[1] * (P(2, 1, 0) + P(0, 3, 0) + P(0, 1, 2)) +
+                       q[2] * (P(2, 0, 1) + P(0, 2, 1) + P(0, 0, 3));
+    const double cq1 = q[0] * P(1, 0, 0) + q[1] * P(0, 1, 0) + q[2] * P(0, 0, 1);
+    const double k = (1.0 - Pr) / (5.0 * p * RT);
+    const double F = A * (P(0, 0, 0) + k * (cq3 / RT - 5.0 * cq1));
     if (lane == 0) rho_w[idx] = F * wall_norm[kind * 6 + s];
 }
 
@@ -419,11 +441,11 @@ cudaError_t launch_finalize_residual(const double *blk_res, const int *blk_bad, 
 }
 
 cudaError_t launch_wall_flux_init(const double *mac, const int8_t *wall_kind, const double *wall_norm,
-                                  const double *vel64, int Nv, unsigned long long ncell, double R, double Pr,
-                                  double *rho_w, cudaStream_t s)
+                                  const double *axis64, int nvx, int nvy, int nvz, unsigned long long ncell, double R,
+                                  double Pr, double *rho_w, cudaStream_t s)
 {
-    wall_flux_init_kernel<<<nblk(6 * ncell, 4), 128, 0, s>>>(mac, wall_kind, wall_norm, vel64, Nv, ncell, R, Pr,
-                                                              rho_w);
+    wall_flux_init_kernel<<<nblk(6 * ncell, 4), 128, 0, s>>>(mac, wall_kind, wall_norm, axis64, nvx, nvy, nvz, ncell, R,
+                                                              Pr, rho_w);
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ struct kgs_ctx {
     void *coef = nullptr, *vel = nullptr, *velm = nullptr, *mtab = nullptr, *FX = nullptr, *FY = nullptr,
          *FZ = nullptr;
     void *part = nullptr;
-    double *vel64 = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;
+    double *vel64 = nullptr, *axis64 = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;
     double *ddx = nullptr, *ddy = nullptr, *ddz = nullptr;
     uint8_t *solid = nullptr, *side_flags = nullptr;
     int8_t *wall_kind = nullptr;

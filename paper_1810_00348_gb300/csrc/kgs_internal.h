@@ -176,7 +176,8 @@ cudaError_t launch_scale_residual(double *mac_new, double *rho_w_new, const doub
 cudaError_t launch_finalize_residual(const double *blk_res, const int *blk_bad, int n_blocks, double *out2,
                                      cudaStream_t s);
 cudaError_t launch_wall_flux_init(const double *mac, const int8_t *wall_kind, const double *wall_norm,
-                                  const double *vel64, int Nv, unsigned long long ncell, double R, double Pr,
+                                  const double *axis64, int nvx, int nvy, int nvz, unsigned long long ncell, double R,
+                                  double Pr,
                                   double *rho_w, cudaStream_t s);
 cudaError_t launch_fill(double *p, unsigned long long n, double v, cudaStream_t s);
 

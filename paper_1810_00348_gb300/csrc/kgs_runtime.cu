@@ -125,7 +125,8 @@ int initial_state(kgs_ctx *c, const double *macros)
     }
     c->M0 = M0;
     KGS_CHECK(cudaMemcpyAsync(c->mac, m.data(), sizeof(double) * 8 * n, cudaMemcpyHostToDevice, c->stream));
-    KGS_CHECK(launch_wall_flux_init(c->mac, c->wall_kind, c->wall_norm, c->vel64, t.Nv, n, R_GAS, t.Pr, c->rho_w,
+    KGS_CHECK(launch_wall_flux_init(c->mac, c->wall_kind, c->wall_norm, c->axis64, t.nvx, t.nvy, t.nvz, n, R_GAS, t.Pr,
+                                    c->rho_w,
                                     c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     c->iteration = 0;
@@ -396,7 +397,7 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
     c->n_red_blocks = (int)((n + 255) / 256);
     if ((rc = dalloc_t(c, &c->mac, 8 * n)) || (rc = dalloc_t(c, &c->mac_new, 8 * n)) ||
         (rc = dalloc_t(c, &c->rho_w, 6 * n)) || (rc = dalloc_t(c, &c->rho_w_new, 6 * n)) ||
-        (rc = dalloc(c, &c->coef, n * NCOEF * rsz)) || (rc = upload(c, &c->vel64, t.vel64)) ||
+        (rc = dalloc(c, &c->coef, n * NCOEF * rsz)) || (rc = upload(c, &c->vel64, t.vel64)) || (rc = upload(c, &c->axis64, t.axis64)) ||
         (rc = upload_real(c, &c->vel, t.vel64)) || (rc = upload_real(c, &c->mtab, t.mt)) ||
         (rc = dalloc(c, &c->FX, (size_t)t.nz * t.ny * t.Nv * rsz)) ||
         (rc = dalloc(c, &c->FY, (size_t)t.nz * t.nx * t.Nv * rsz)) ||

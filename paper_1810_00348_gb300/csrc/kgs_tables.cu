@@ -124,6 +124,13 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
         t.oct_nx[o] = cnt;
         t.nxo_max = std::max(t.nxo_max, cnt);
     }
+    t.axis64.clear();
+    t.axis64.insert(t.axis64.end(), vg->xi_x, vg->xi_x + t.nvx);
+    t.axis64.insert(t.axis64.end(), vg->xi_y, vg->xi_y + t.nvy);
+    t.axis64.insert(t.axis64.end(), vg->xi_z, vg->xi_z + t.nvz);
+    t.axis64.insert(t.axis64.end(), vg->w_x, vg->w_x + t.nvx);
+    t.axis64.insert(t.axis64.end(), vg->w_y, vg->w_y + t.nvy);
+    t.axis64.insert(t.axis64.end(), vg->w_z, vg->w_z + t.nvz);
     t.vel64.assign((size_t)t.Nv * 4, 0.0);
     t.velm64.assign((size_t)t.Nv * 8, 0.0);
     t.velm32.assign((size_t)t.Nv * 8, 0.f);

@@ -28,6 +28,7 @@ struct HostTables {
     int n_vg = 0, max_vg = 0, nxo_max = 1;
     std::vector<int> vg_oct;                 // octant of each velocity group
     std::vector<double> vel64;               // [Nv][4] xi_x, xi_y, xi_z, w
+    std::vector<double> axis64;              // 1D nodes and weights: xi_x, xi_y, xi_z, w_x, w_y, w_z
     std::vector<double> velm64;              // [Nv][8] w_x, w_y w_z, 0 ...
     std::vector<float> velm32;               // [Nv][8] w_x, w_y w_z, low parts of xi
     std::vector<double> mt;                  // [MT_ROWS][Nv] wall Maxwellians, free stream
