@@ -139,16 +139,37 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
             // FP32 partials are compensated pairs (value = x - y); they are
             // summed as float-float numbers (hi + lo, hi updated by an error-
             // free two-sum) on the FP32 pipe and widened once at the end
-            FFSum acc[2];
+            // The loads go in batches of CB groups into registers, the next
+            // batch issued before the current one is summed, so that up to
+            // 2 CB loads per thread are in flight.
+            constexpr int CB = 16;
+            FFSum acc0, acc1;  // flux slots: walls behind / ahead of the group's octant
             const float2 *pp = static_cast<const float2 *>(a.part) + c * NPART + q;
-#pragma unroll 16
-            for (int g = 0; g < a.n_vg; g++) {  // 16 loads in flight per thread
-                const float2 e = pp[(size_t)g * ncell * NPART];
-                const int side = q < P_FX ? 0 : ((a.vg_oct[g] >> axis) & 1);
-                acc[side].add(e.x, e.y);
+            const size_t gs = ncell * NPART;
+            const int n_vg = a.n_vg;
+            float2 cur[CB], nxt[CB];
+            auto load = [&](float2 (&e)[CB], int g0) {
+#pragma unroll
+                for (int k = 0; k < CB; k++) e[k] = g0 + k < n_vg ? pp[(size_t)(g0 + k) * gs] : make_float2(0.f, 0.f);
+            };
+            load(cur, 0);
+            for (int g0 = 0; g0 < n_vg; g0 += CB) {
+                if (g0 + CB < n_vg) load(nxt, g0 + CB);
+#pragma unroll
+                for (int k = 0; k < CB; k++) {
+                    const int g = g0 + k;
+                    if (g < n_vg) {
+                        if (q >= P_FX && ((a.vg_oct[g] >> axis) & 1))
+                            acc1.add(cur[k].x, cur[k].y);
+                        else
+                            acc0.add(cur[k].x, cur[k].y);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < CB; k++) cur[k] = nxt[k];
             }
-            sum = f_minus = acc[0].value();
-            f_plus = acc[1].value();
+            sum = f_minus = acc0.value();
+            f_plus = acc1.value();
         }
         if (q < P_FX) {
             sS[cl][q] = sum;
