@@ -25,6 +25,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -134,10 +136,25 @@ def dist_env():
     return world, rank, local
 
 
-def time_oracle_sample():
+def rel_errors(got, ref):
+    """Largest relative field errors: rho and T pointwise, U and q normalised
+    by the largest magnitude of the reference field (they pass through zero)."""
+    g = np.asarray(got).reshape(8, -1)
+    r = np.asarray(ref).reshape(8, -1)
+    err = {"rho": float(np.max(np.abs(g[0] - r[0]) / np.abs(r[0]))),
+           "T": float(np.max(np.abs(g[4] - r[4]) / np.abs(r[4])))}
+    for name, sl in (("U", slice(1, 4)), ("q", slice(5, 8))):
+        err[name] = float(np.max(np.abs(g[sl] - r[sl])) / max(np.max(np.abs(r[sl])), 1e-300))
+    # the scales of the two normalised fields (q is small early in a run)
+    err["ref_max_abs"] = {"U": float(np.max(np.abs(r[1:4]))), "q": float(np.max(np.abs(r[5:8])))}
+    return err
+
+
+def time_oracle_sample(kgs=None):
     """Oracle (plain serial FP64 C) on a bounded sample of the workload: the
     64^3-cell cavity with an 8^3 velocity grid (one outer iteration, about 15 s
-    on one core)."""
+    on one core).  Given the library, the GPU FP64 and mixed paths run the
+    same iteration and their errors against the oracle's result are reported."""
     from oracle import Oracle
     from paper_1810_00348_gb300 import inputs
 
@@ -147,9 +164,18 @@ def time_oracle_sample():
     o.iterate()
     dt = time.perf_counter() - t0
     pp = prob.phase_points()
-    return {"value": pp / dt, "unit": "phase-point updates/s", "cores": 1, "kind": "oracle",
-            "sample": "one outer iteration of the 64^3-cell cavity with an 8^3 velocity grid "
-                      "(%d phase points, %.1f s on one host core)" % (pp, dt)}
+    out = {"value": pp / dt, "unit": "phase-point updates/s", "cores": 1, "kind": "oracle",
+           "sample": "one outer iteration of the 64^3-cell cavity with an 8^3 velocity grid "
+                     "(%d phase points, %.1f s on one host core)" % (pp, dt)}
+    if kgs is not None:
+        ref = o.macros()
+        out["gpu_error_vs_oracle"] = {}
+        for name, prec in (("fp64", kgs.KGS_FP64), ("mixed", kgs.KGS_MIXED)):
+            c = kgs.kgs_setup(prob, precision=prec)
+            kgs.kgs_iterate(c, 1)
+            out["gpu_error_vs_oracle"][name] = rel_errors(kgs.kgs_moments(c), ref)
+            del c
+    return out
 
 
 def run_reference(args, world, rank):
@@ -271,6 +297,19 @@ def run_ours(args, world, rank, local):
                 "roofline": {"bound": "alu", "achieved": a64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                              "frac": a64 / FP64_PEAK_TFLOPS, "peak_basis": "nominal dense FP64 1.25 TFLOP/s"}}
         del c64
+        if rank == 0 and args.cells == N_CELL and args.vels == N_VEL:
+            # mixed against FP64 at the full size after two iterations from the
+            # uniform start, for both Knudsen numbers of the workload family
+            fp64["mixed_vs_fp64_after_2_iterations"] = {}
+            for kn in (KN, 0.1):
+                pk = inputs.cavity(N_CELL, N_VEL, Kn=kn, lid=LID)
+                m = {}
+                for prec in (kgs.KGS_FP64, kgs.KGS_MIXED):
+                    c = kgs.kgs_setup(pk, precision=prec, block_z=args.block_z)
+                    kgs.kgs_iterate(c, 2)
+                    m[prec] = kgs.kgs_moments(c)
+                    del c
+                fp64["mixed_vs_fp64_after_2_iterations"]["Kn=%g" % kn] = rel_errors(m[kgs.KGS_MIXED], m[kgs.KGS_FP64])
 
     extras = {}
     if not args.no_extras:
@@ -282,7 +321,7 @@ def run_ours(args, world, rank, local):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = time_oracle_sample()
+        cpu = time_oracle_sample(kgs)
     line = {
         "metric": METRIC, "value": value, "unit": "phase-point updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,

@@ -52,6 +52,21 @@ def test_cavity64_mixed_matches_fp64(kgs, cavity64):
     assert max(err.values()) <= 1e-5, err
 
 
+def test_cavity64_kn01_mixed_matches_fp64(kgs):
+    # the second Knudsen number of the 64^3 x 32^3 workload family: collisions
+    # dominate, the equilibrium term is ten times stiffer
+    p = inputs.cavity(64, 32, Kn=0.1, lid=0.16)
+    m = {}
+    for prec in (kgs.KGS_FP64, kgs.KGS_MIXED):
+        ctx = kgs.kgs_setup(p, precision=prec)
+        rc, n, res = kgs.kgs_iterate(ctx, 2)
+        assert rc == kgs.KGS_OK
+        m[prec] = kgs.kgs_moments(ctx)
+    err = field_errors(m[kgs.KGS_MIXED], m[kgs.KGS_FP64])
+    assert max(err.values()) <= 1e-5, err
+    assert mirror_errors(m[kgs.KGS_FP64], 2) < 1e-12
+
+
 def test_cavity64_z_mirror_symmetry_and_mass(kgs, cavity64):
     p, out = cavity64
     m64 = out[kgs.KGS_FP64][0]
