@@ -57,6 +57,8 @@ def _load():
         lib.kgso_equilibrium.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p]
         lib.kgso_moments.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p]
         lib.kgso_sweep.argtypes = [ctypes.c_void_p, ctypes.c_int, _dbl_p]
+        lib.kgso_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.kgso_parallel.restype = ctypes.c_int
         lib.kgso_ghost.restype = ctypes.c_double
         lib.kgso_ghost.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         _lib = lib
@@ -72,9 +74,11 @@ def _f64(a):
 
 
 class Oracle:
-    """One oracle solver state built from an ``inputs.Problem``."""
+    """One oracle solver state built from an ``inputs.Problem``.  ``threads``
+    > 1 sweeps that many contiguous velocity ranges concurrently, with private
+    sums added in range order (same arithmetic, another summation order)."""
 
-    def __init__(self, prob, macros0=None):
+    def __init__(self, prob, macros0=None, threads=1):
         lib = _load()
         self.prob = prob
         self._keep = []
@@ -111,6 +115,7 @@ class Oracle:
         self._s = lib.kgso_create(ctypes.byref(P), _ptr(m0) if m0 is not None else _dbl_p())
         if not self._s:
             raise ValueError("oracle rejected the problem")
+        lib.kgso_set_threads(self._s, int(threads))
         self.ncell = prob.nx * prob.ny * prob.nz
         self.nvel = P.nvx * P.nvy * P.nvz
 
@@ -164,3 +169,8 @@ class Oracle:
 
     def ghost(self, c, face, a):
         return _load().kgso_ghost(self._s, int(c), int(face), int(a))
+
+
+def parallel_build() -> bool:
+    """The oracle library runs its optional velocity ranges on several threads."""
+    return bool(_load().kgso_parallel())

@@ -42,6 +42,7 @@ struct kgso_state {
     double mu_ref;
     double M0;      /* initial total mass                          */
     double out_flux_unit[7][6]; /* discrete-mode normaliser, per wall kind and face */
+    int threads;    /* velocity ranges swept concurrently (1: plain serial loop) */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -367,6 +368,7 @@ kgso_state *kgso_create(const kgso_problem *p, const double *macros0)
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nvx < 1 || p->nvy < 1 || p->nvz < 1) return NULL;
     kgso_state *s = (kgso_state *)calloc(1, sizeof(kgso_state));
     s->p = *p;
+    s->threads = 1;
     s->ncell = p->nx * p->ny * p->nz;
     s->nvel = p->nvx * p->nvy * p->nvz;
     s->dx = copy_array(p->dx, p->nx);
@@ -461,6 +463,62 @@ void kgso_set_rho_w(kgso_state *s, const double *in)
 /* ------------------------------------------------------------------------ */
 /* one outer iteration, Eq. (6) + Algorithm 1                               */
 
+/* Sums of one outer iteration's first pass over velocities [a0, a1): each
+ * velocity is swept into f with the lagged f^{S,n}, tau^n and rho_w^n and
+ * added to rho, rho U, rho E (Eq. (5)) and to the incoming wall fluxes of
+ * Eq. (9). */
+static void pass1(const kgso_state *s, int a0, int a1, double *f, double *rho, double *mom, double *rhoE, double *F)
+{
+    const int nc = s->ncell;
+    for (int a = a0; a < a1; a++) {
+        double xi[3], w;
+        velocity(s, a, xi, &w);
+        kgso_sweep(s, a, f);
+        double xi2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+        for (int c = 0; c < nc; c++) {
+            if (is_solid(s, c)) continue;
+            double fc = f[c];
+            rho[c] += w * fc;
+            for (int d = 0; d < 3; d++) mom[(size_t)d * nc + c] += w * xi[d] * fc;
+            rhoE[c] += 0.5 * w * xi2 * fc;
+            for (int face = 0; face < 6; face++)
+                if (is_wall_face(s, c, face)) F[(size_t)face * nc + c] += incoming_flux(face, xi, w, fc);
+        }
+    }
+}
+
+/* Second pass over velocities [a0, a1): q = 1/2 sum w c |c|^2 f with
+ * c = xi - U^{n+1} (Eq. (5)), from the same sweeps. */
+static void pass2(const kgso_state *s, int a0, int a1, double *f, const double *U, double *q)
+{
+    const int nc = s->ncell;
+    for (int a = a0; a < a1; a++) {
+        double xi[3], w;
+        velocity(s, a, xi, &w);
+        kgso_sweep(s, a, f);
+        for (int c = 0; c < nc; c++) {
+            if (is_solid(s, c)) continue;
+            double cc[3], c2 = 0.0;
+            for (int d = 0; d < 3; d++) {
+                cc[d] = xi[d] - U[(size_t)d * nc + c];
+                c2 += cc[d] * cc[d];
+            }
+            for (int d = 0; d < 3; d++) q[(size_t)d * nc + c] += 0.5 * w * cc[d] * c2 * f[c];
+        }
+    }
+}
+
+void kgso_set_threads(kgso_state *s, int n) { s->threads = n > 1 ? n : 1; }
+
+int kgso_parallel(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 double kgso_iterate(kgso_state *s)
 {
     const int nc = s->ncell;
@@ -475,20 +533,31 @@ double kgso_iterate(kgso_state *s)
     /* Pass 1: each velocity in turn is swept with the lagged f^{S,n}, tau^n and
      * rho_w^n, and its contribution is added to rho, rho U, rho E (Eq. (5))
      * and to the incoming wall fluxes of Eq. (9). */
-    for (int a = 0; a < s->nvel; a++) {
-        double xi[3], w;
-        velocity(s, a, xi, &w);
-        kgso_sweep(s, a, s->f);
-        double xi2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
-        for (int c = 0; c < nc; c++) {
-            if (is_solid(s, c)) continue;
-            double fc = s->f[c];
-            rho[c] += w * fc;
-            for (int d = 0; d < 3; d++) mom[(size_t)d * nc + c] += w * xi[d] * fc;
-            rhoE[c] += 0.5 * w * xi2 * fc;
-            for (int face = 0; face < 6; face++)
-                if (is_wall_face(s, c, face)) F[(size_t)face * nc + c] += incoming_flux(face, xi, w, fc);
+    if (s->threads <= 1) {
+        pass1(s, 0, s->nvel, s->f, rho, mom, rhoE, F);
+    } else {
+        /* optional: contiguous velocity ranges with private sums, added up in
+         * range order afterwards */
+        const int T = s->threads;
+        double *f_t = (double *)calloc((size_t)T * nc, sizeof(double));
+        double *acc = (double *)calloc((size_t)T * 11 * nc, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+#endif
+        for (int t = 0; t < T; t++) {
+            double *a_t = acc + (size_t)t * 11 * nc;
+            pass1(s, (int)((long long)s->nvel * t / T), (int)((long long)s->nvel * (t + 1) / T), f_t + (size_t)t * nc,
+                  a_t, a_t + nc, a_t + 4 * (size_t)nc, a_t + 5 * (size_t)nc);
         }
+        for (int t = 0; t < T; t++) {
+            const double *a_t = acc + (size_t)t * 11 * nc;
+            for (size_t i = 0; i < (size_t)nc; i++) rho[i] += a_t[i];
+            for (size_t i = 0; i < (size_t)3 * nc; i++) mom[i] += a_t[nc + i];
+            for (size_t i = 0; i < (size_t)nc; i++) rhoE[i] += a_t[4 * (size_t)nc + i];
+            for (size_t i = 0; i < (size_t)6 * nc; i++) F[i] += a_t[5 * (size_t)nc + i];
+        }
+        free(acc);
+        free(f_t);
     }
     for (int c = 0; c < nc; c++) {
         if (is_solid(s, c)) continue;
@@ -497,19 +566,22 @@ double kgso_iterate(kgso_state *s)
     /* Pass 2: the heat flux of Eq. (5) needs the new U, so every velocity is
      * swept again (the sweep is deterministic) and q = 1/2 sum w c c^2 f is
      * accumulated with c = xi - U^{n+1}. */
-    for (int a = 0; a < s->nvel; a++) {
-        double xi[3], w;
-        velocity(s, a, xi, &w);
-        kgso_sweep(s, a, s->f);
-        for (int c = 0; c < nc; c++) {
-            if (is_solid(s, c)) continue;
-            double cc[3], c2 = 0.0;
-            for (int d = 0; d < 3; d++) {
-                cc[d] = xi[d] - U[(size_t)d * nc + c];
-                c2 += cc[d] * cc[d];
-            }
-            for (int d = 0; d < 3; d++) q[(size_t)d * nc + c] += 0.5 * w * cc[d] * c2 * s->f[c];
-        }
+    if (s->threads <= 1) {
+        pass2(s, 0, s->nvel, s->f, U, q);
+    } else {
+        const int T = s->threads;
+        double *f_t = (double *)calloc((size_t)T * nc, sizeof(double));
+        double *acc = (double *)calloc((size_t)T * 3 * nc, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+#endif
+        for (int t = 0; t < T; t++)
+            pass2(s, (int)((long long)s->nvel * t / T), (int)((long long)s->nvel * (t + 1) / T), f_t + (size_t)t * nc,
+                  U, acc + (size_t)t * 3 * nc);
+        for (int t = 0; t < T; t++)
+            for (size_t i = 0; i < (size_t)3 * nc; i++) q[i] += acc[(size_t)t * 3 * nc + i];
+        free(acc);
+        free(f_t);
     }
 
     int bad = 0;

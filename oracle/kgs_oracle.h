@@ -57,6 +57,13 @@ void kgso_destroy(kgso_state *s);
  * number if the new state is not physical (NaN, rho <= 0 or T <= 0). */
 double kgso_iterate(kgso_state *s);
 
+/* Optional: sweep n contiguous velocity ranges concurrently (OpenMP when the
+ * library was built with it), each with private sums that are added in range
+ * order; 1 (the default) is the plain serial loop.  kgso_parallel() tells
+ * whether the build runs the ranges on several threads. */
+void kgso_set_threads(kgso_state *s, int n);
+int kgso_parallel(void);
+
 void kgso_get_macros(const kgso_state *s, double *out);    /* [8][ncell] */
 void kgso_get_rho_w(const kgso_state *s, double *out);     /* [6][ncell] */
 void kgso_set_rho_w(kgso_state *s, const double *in);      /* [6][ncell] */

@@ -402,3 +402,17 @@ def test_mass_rescale_scales_rho_q_and_wall_density_only():
     np.testing.assert_allclose(m1[5:8], s * m0[5:8], rtol=1e-12, atol=1e-16)
     np.testing.assert_allclose(m1[1:5], m0[1:5], rtol=1e-13, atol=1e-16)
     np.testing.assert_allclose(rw1, s * rw0, rtol=1e-13)
+
+
+def test_concurrent_velocity_ranges_match_the_serial_loop():
+    # the optional concurrent ranges change only the order in which the
+    # per-velocity contributions are added
+    from tests.parity import field_errors
+    p = inputs.cavity([9, 7, 10], 12, Kn=0.5, lid=0.2)
+    mac = inputs.random_macros(p, 5)
+    serial, ranged = Oracle(p, mac), Oracle(p, mac, threads=4)
+    serial.iterate(2)
+    ranged.iterate(2)
+    err = field_errors(ranged.macros(), serial.macros())
+    assert max(err.values()) < 1e-12, err
+    assert np.max(np.abs(ranged.rho_w() - serial.rho_w())) < 1e-12
