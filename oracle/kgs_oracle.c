@@ -17,6 +17,9 @@
  *   Eq. (10) reference viscosity from the Knudsen number,
  *   Sec. 4.1 convergence monitor (relative L2 change of rho, rho U, rho E).
  * Readings of silent or garbled passages are listed where they are used.
+ * The serial loop over velocities is the default; an optional mode sweeps
+ * contiguous velocity ranges concurrently and adds their private sums in
+ * range order (kgso_set_threads), for comparisons at full workload sizes.
  *
  * Parity status: every function here is pinned by the CPU tests (closed-form
  * quadrature moments, dense linear solves of the sweep, rest state, mass,
@@ -25,6 +28,9 @@
 #include "kgs_oracle.h"
 
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
