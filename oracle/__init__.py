@@ -1,7 +1,7 @@
 """ctypes front end of the FP64 CPU oracle (test infrastructure only).
 
-The oracle is a plain C solver of the paper's equations (serial by default) (arXiv
-1810.00348, Eqs. (2)-(10), Algorithm 1).  Only the tests, the smoke check and
+The oracle is a plain C solver, serial by default, of the paper's equations
+(arXiv 1810.00348, Eqs. (2)-(10), Algorithm 1).  Only the tests, the smoke check and
 the CPU-baseline leg of the benchmark import this module.  It does not import
 the CUDA package and the CUDA package does not import it; both take their
 inputs from ``paper_1810_00348_gb300.inputs``, which holds no solver arithmetic.
