@@ -84,11 +84,17 @@ def test_forward_matches_reference(kgs, channels, shape):
         assert np.abs(y[b] - ref).max() <= 2e-3 * scale, (b, np.abs(y[b] - ref).max(), scale)
 
 
-@pytest.mark.parametrize("channels,shape,masked", [
-    ((11, 16, 112, 32, 8), (2, 5, 6, 7), False),
-    ((11, 16, 8), (1, 20, 20, 20), True),     # 125 voxel tiles: several weight-gradient chunks
+# Relative L2 errors of the weight and bias gradients per layer.  Both sides
+# round activations and propagated gradients to bf16, in different orders;
+# measured: at most 2.6e-3 on the first two cases, 1.6e-2 on the first layer
+# of the full six-layer network (the rounding differences accumulate over
+# the depth of the backward pass).
+@pytest.mark.parametrize("channels,shape,masked,tol", [
+    ((11, 16, 112, 32, 8), (2, 5, 6, 7), False, 1e-2),
+    ((11, 16, 8), (1, 20, 20, 20), True, 1e-2),     # 125 voxel tiles: several weight-gradient chunks
+    ((11, 48, 112, 112, 112, 48, 8), (2, 16, 16, 16), False, 5e-2),  # the network the solver uses
 ])
-def test_gradients_match_reference(kgs, channels, shape, masked):
+def test_gradients_match_reference(kgs, channels, shape, masked, tol):
     params = random_params(channels, seed=3)
     net = kgs.kgs_net_create(channels, seed=0)
     kgs.kgs_net_set_params(net, flat(params))
@@ -119,7 +125,7 @@ def test_gradients_match_reference(kgs, channels, shape, masked):
     for l, ((gW, gb), (rW, rb)) in enumerate(zip(g, ref_g)):
         eW = np.linalg.norm(gW - rW) / np.linalg.norm(rW)
         eb = np.linalg.norm(gb - rb) / np.linalg.norm(rb)
-        assert eW <= 5e-2 and eb <= 5e-2, (l, eW, eb)
+        assert eW <= tol and eb <= tol, (l, eW, eb)
 
 
 def test_training_reduces_loss(kgs):
