@@ -258,14 +258,16 @@ __global__ void __launch_bounds__(THREADS, 1)
             s_last = t;
         }
         tc_commit(smem_u32(&done_bar));  // all MMAs issued by this thread
+        // all MMAs of the CTA are complete once the done barrier has fired.
+        // Only this thread waits for it; the others are parked at the CTA
+        // barrier below instead of polling beside the two pipeline threads.
+        if (!mbar_wait(smem_u32(&done_bar), 0)) *fail = 1;
     }
-    // all MMAs of the CTA are complete once the done barrier has fired; the
-    // verdict is made uniform because the loads below are warp-collective
-    const bool done = __syncthreads_and(mbar_wait(smem_u32(&done_bar), 0)) != 0;
+    __syncthreads();  // the verdict in s_fail / s_last is uniform after it
     const int last = s_last;
     const uint32_t tmem = tmem_base;
     tc_fence_after();
-    if (!done || s_fail || last != 26) {
+    if (s_fail || last != 26) {
         if (threadIdx.x == 0) atomicExch(err, 1);
     } else {
         const int row = warp * 32 + lane;
