@@ -2,24 +2,30 @@
 // generation tensor cores (tcgen05.mma, accumulator in tensor memory).
 //
 // GEMM view: out[v][co] = sum over taps t and input channels ci of
-// in[v + off(t)][ci] W[t][co][ci].  A CTA owns 128 output voxels, an 8 (x)
-// by 16 (y) patch of one z-plane, i.e. the M = 128 rows of one MMA, and all
-// output channels (N = cout_p <= 112).  It stages the input halo of the
-// patch (10 x 18 x 3 voxels, all channels) in shared memory once, in the
-// K-major no-swizzle layout the MMA reads: 16-byte rows (8 channels of one
-// voxel), x fastest within a channel octet, so that for every tap the 8 x
-// positions of an output row segment are 8 consecutive 16-byte rows (one
-// 8 x 16 B core matrix) and the 16 y rows and the channel octets are fixed
-// strides.  Each tap is then C/16 MMAs of 128 x N x 16 reading shifted
-// windows of the same halo; no im2col copy is made.  The halo moves with
-// cp.async.  The weights, packed beforehand so that a tap is one contiguous
-// block in the layout the MMA reads, move with one bulk copy per tap into a
-// ring of four buffers.  Two threads drive the pipeline without CTA-wide
-// barriers: a producer issues the copy of tap t once the MMAs of tap t-4 have
-// released its buffer (commit barrier), and an issuer starts the MMAs of tap
-// t once its copy has landed (transaction barrier).  The epilogue reads the accumulator with tcgen05.ld (warp w owns
-// TMEM lanes 32w..32w+31 = output rows) and applies bias + ReLU, bias only,
-// or the ReLU mask of the backward pass.
+// in[v + off(t)][ci] W[t][co][ci].  A CTA owns an 8 (x) by 16 (y) patch of two
+// consecutive z-planes: two accumulators of M = 128 rows (voxels) each, all
+// output channels (N = cout_p <= 112), so every weight tile that reaches
+// shared memory feeds the MMAs of both planes.  The input planes z0 - 1 ..
+// z0 + 2 (10 x 18 voxels, all channels each) go through a ring of three
+// slots in the K-major no-swizzle layout the MMA reads: 16-byte rows (8
+// channels of one voxel), x fastest within a channel octet, so that for every
+// tap the 8 x positions of an output row segment are 8 consecutive 16-byte
+// rows (one 8 x 16 B core matrix) and the 16 y rows and the channel octets
+// are fixed strides.  Each tap is then C/16 MMAs of 128 x N x 16 per plane
+// reading shifted windows of the staged planes; no im2col copy is made.  The
+// planes move with cp.async: the first two before the pipeline starts, the
+// third and fourth by two loader warps while the tensor core works (the
+// fourth reuses the first's slot once the taps kz = 0 are done).  The
+// weights, packed beforehand so that a tap is one contiguous block in the
+// layout the MMA reads, move with one bulk copy per tap into a ring of four
+// buffers.  Two threads drive the pipeline without CTA-wide barriers: a
+// producer issues the copy of tap t once the MMAs of tap t-4 have released
+// its buffer (commit barrier), and an issuer starts the MMAs of tap t once
+// its copy has landed (transaction barrier); the remaining threads wait at a
+// CTA barrier, not polling, until the issuer has seen the last MMA complete.
+// The epilogue reads the accumulators with tcgen05.ld (warp w owns TMEM lanes
+// 32w..32w+31 = output rows) and applies bias + ReLU, bias only, or the ReLU
+// mask of the backward pass.
 //
 // The weight gradient (wgrad_tc_kernel) is the per-tap GEMM dW[t][co][ci] =
 // sum over voxels v of dy[v][co] in[v + off(t)][ci] with the voxels as the
@@ -42,9 +48,12 @@ namespace nn {
 namespace {
 
 constexpr int TX = 8, TY = 16;                 // output patch: 128 voxels = 128 GEMM rows
-constexpr int HX = TX + 2, HY = TY + 2, HZ = 3;  // input halo of the patch
+constexpr int HX = TX + 2, HY = TY + 2, HZ = 3;  // input plane of the patch; ring of HZ plane slots
 constexpr int THREADS = 128;
-constexpr int TMEM_COLS = 128;                 // >= N, a power of two
+constexpr int OZ = 2;                          // output planes per CTA (two accumulators)
+constexpr int TMEM_HALF = 128;                 // columns of one accumulator (>= N)
+constexpr int TMEM_COLS = OZ * TMEM_HALF;      // a power of two
+constexpr int LOADERS = 64;                    // threads that stream the later input planes
 constexpr int NBUF = 4;                        // weight buffers: up to four taps in flight
 constexpr long long WAIT_POLLS = 1ll << 20;    // try_wait polls before giving up
 
@@ -98,6 +107,11 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool v
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 {
@@ -165,27 +179,43 @@ __global__ void __launch_bounds__(THREADS, 1)
                    int *err)
 {
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ __align__(8) uint64_t full_bar[NBUF], empty_bar[NBUF], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[NBUF], empty_bar[NBUF], done_bar, plane_full[2], plane_empty;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail, s_last;  // a wait gave up; last tap whose MMAs were committed
 
     const int C8 = dm.cin_p / 8, cout_p = dm.cout_p;
-    const size_t halo_bytes = (size_t)HZ * HY * C8 * HX * 16;
+    const uint32_t plane_bytes = (uint32_t)HY * C8 * HX * 16;
     const uint32_t w_bytes = (uint32_t)C8 * cout_p * 16;
-    unsigned char *halo = sm;
-    unsigned char *wbuf = sm + halo_bytes;
+    unsigned char *wbuf = sm + HZ * plane_bytes;
     const int tiles_x = (dm.W + TX - 1) / TX;
     const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
-    const int z = blockIdx.y, b = blockIdx.z;
+    const int z0 = blockIdx.y * OZ, b = blockIdx.z;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     auto full = [&](int t) { return smem_u32(&full_bar[t % NBUF]); };    // weights of tap t landed
     auto empty = [&](int t) { return smem_u32(&empty_bar[t % NBUF]); };  // MMAs of tap t done
     auto use = [](int t) { return (uint32_t)((t / NBUF) & 1); };         // phase parity of tap t's use
-    const uint32_t halo_a = smem_u32(halo), w_a = smem_u32(wbuf);
-    volatile int *fail = &s_fail;  // written by the two pipeline threads
+    const uint32_t halo_a = smem_u32(sm), w_a = smem_u32(wbuf);
+    volatile int *fail = &s_fail;  // written by the pipeline threads
     auto issue_w = [&](int t) {  // bulk copy of tap t into buffer t % NBUF
         mbar_expect_tx(full(t), w_bytes);
         bulk_copy(w_a + (uint32_t)(t % NBUF) * w_bytes, wpk + (size_t)t * cout_p * dm.cin_p, w_bytes, full(t));
+    };
+    // input plane p (z = z0 - 1 + p, p = 0..3) in slot p % 3: element (hx, hy,
+    // channel octet c8) at ((hy * C8 + c8) * HX + hx) * 16
+    const size_t vol = (size_t)dm.D * dm.H * dm.W;
+    auto load_plane = [&](int p, int first, int stride) {
+        const int gz = z0 - 1 + p;
+        const uint32_t dst = halo_a + (uint32_t)(p % HZ) * plane_bytes;
+        for (int i = first; i < HY * HX * C8; i += stride) {
+            const int c8 = i % C8, r = i / C8;
+            const int hx = r % HX, hy = r / HX;
+            const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+            const bool valid = gx >= 0 && gy >= 0 && gz >= 0 && gx < dm.W && gy < dm.H && gz < dm.D;
+            const __nv_bfloat16 *src =
+                valid ? in + ((size_t)b * vol + ((size_t)gz * dm.H + gy) * dm.W + gx) * dm.cin_p + c8 * 8 : in;
+            cp_async16(dst + (uint32_t)((hy * C8 + c8) * HX + hx) * 16, src, valid);
+        }
+        cp_async_commit();
     };
 
     if (threadIdx.x == 0) {
@@ -194,6 +224,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(smem_u32(&empty_bar[q]), 1);
         }
         mbar_init(smem_u32(&done_bar), 1);
+        mbar_init(smem_u32(&plane_full[0]), LOADERS);
+        mbar_init(smem_u32(&plane_full[1]), LOADERS);
+        mbar_init(smem_u32(&plane_empty), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
         s_last = -1;
@@ -206,19 +239,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-
-    // input halo: element (hx, hy, hz, channel octet c8) at ((hz*HY + hy)*C8 + c8)*HX + hx
-    const size_t vol = (size_t)dm.D * dm.H * dm.W;
-    for (int i = threadIdx.x; i < HZ * HY * HX * C8; i += THREADS) {
-        const int c8 = i % C8, r = i / C8;
-        const int hx = r % HX, hy = (r / HX) % HY, hz = r / (HX * HY);
-        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z - 1 + hz;
-        const bool valid = gx >= 0 && gy >= 0 && gz >= 0 && gx < dm.W && gy < dm.H && gz < dm.D;
-        const __nv_bfloat16 *src =
-            valid ? in + ((size_t)b * vol + ((size_t)gz * dm.H + gy) * dm.W + gx) * dm.cin_p + c8 * 8 : in;
-        cp_async16(halo_a + (uint32_t)(((hz * HY + hy) * C8 + c8) * HX + hx) * 16, src, valid);
-    }
-    cp_async_commit();
+    // the first two input planes, by every thread
+    load_plane(0, threadIdx.x, THREADS);
+    load_plane(1, threadIdx.x, THREADS);
     cp_async_wait<0>();
     fence_async_smem();
     tc_fence_before();
@@ -235,33 +258,57 @@ __global__ void __launch_bounds__(THREADS, 1)
             issue_w(t);
         }
     } else if (threadIdx.x == 32) {
-        // MMA issuer: C/16 MMAs of 128 x N x 16 per tap, accumulating in TMEM
+        // MMA issuer: per tap and channel pair, one MMA of 128 x N x 16 for
+        // each output plane, both reading the same weights
         const uint32_t tmem = tmem_base;
         const uint32_t idesc = instr_desc(128, cout_p);
         const uint32_t a_lbo = HX * 16, a_sbo = (uint32_t)C8 * HX * 16;
         const uint32_t b_lbo = (uint32_t)cout_p * 16, b_sbo = 8 * 16;
         for (int t = 0; t < 27; t++) {
-            if (*fail || !mbar_wait(full(t), use(t))) {
+            const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
+            // plane kz + 1 (for the second output plane) first used by the taps kz
+            bool ok = !*fail;
+            if (ok && t == 9) ok = mbar_wait(smem_u32(&plane_full[0]), 0);
+            if (ok && t == 18) ok = mbar_wait(smem_u32(&plane_full[1]), 0);
+            if (!ok || !mbar_wait(full(t), use(t))) {
                 *fail = 1;
                 break;
             }
             tc_fence_after();
-            const int kx = t % 3, ky = (t / 3) % 3, kz = t / 9;
+            const uint32_t pa0 = halo_a + (uint32_t)(kz % HZ) * plane_bytes;        // plane kz: output z0
+            const uint32_t pa1 = halo_a + (uint32_t)((kz + 1) % HZ) * plane_bytes;  // plane kz + 1: output z0 + 1
             for (int kc = 0; kc < C8 / 2; kc++) {
-                const uint64_t a = smem_desc(halo_a + (uint32_t)((((kz * HY + ky) * C8 + 2 * kc) * HX + kx) * 16),
-                                             a_lbo, a_sbo);
+                const uint32_t off = (uint32_t)(((ky * C8 + 2 * kc) * HX + kx) * 16);
                 const uint64_t bd =
                     smem_desc(w_a + (uint32_t)(t % NBUF) * w_bytes + (uint32_t)(2 * kc * cout_p * 16), b_lbo, b_sbo);
-                tc_mma(tmem, a, bd, idesc, (t | kc) != 0);
+                tc_mma(tmem, smem_desc(pa0 + off, a_lbo, a_sbo), bd, idesc, (t | kc) != 0);
+                tc_mma(tmem + TMEM_HALF, smem_desc(pa1 + off, a_lbo, a_sbo), bd, idesc, (t | kc) != 0);
             }
             tc_commit(empty(t));
+            if (t == 8) tc_commit(smem_u32(&plane_empty));  // plane 0 (slot 0) no longer read
             s_last = t;
         }
         tc_commit(smem_u32(&done_bar));  // all MMAs issued by this thread
         // all MMAs of the CTA are complete once the done barrier has fired.
         // Only this thread waits for it; the others are parked at the CTA
-        // barrier below instead of polling beside the two pipeline threads.
+        // barrier below instead of polling beside the pipeline threads.
         if (!mbar_wait(smem_u32(&done_bar), 0)) *fail = 1;
+    } else if (threadIdx.x >= THREADS - LOADERS) {
+        // loaders: plane 2 into slot 2 now, plane 3 into slot 0 once the MMAs
+        // of the taps kz = 0 have released plane 0
+        const int lt = threadIdx.x - (THREADS - LOADERS);
+        load_plane(2, lt, LOADERS);
+        cp_async_wait<0>();
+        fence_async_smem();
+        mbar_arrive(smem_u32(&plane_full[0]));
+        if (mbar_wait(smem_u32(&plane_empty), 0)) {
+            load_plane(3, lt, LOADERS);
+            cp_async_wait<0>();
+            fence_async_smem();
+        } else {
+            *fail = 1;  // the issuer's wait on plane_full[1] then gives up too
+        }
+        mbar_arrive(smem_u32(&plane_full[1]));
     }
     __syncthreads();  // the verdict in s_fail / s_last is uniform after it
     const int last = s_last;
@@ -273,38 +320,42 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int row = warp * 32 + lane;
         const int vx = x0 + row % TX, vy = y0 + row / TX;
         const bool inside = vx < dm.W && vy < dm.H;
-        const size_t vo = (size_t)b * vol + ((size_t)z * dm.H + vy) * dm.W + vx;
-        for (int c0 = 0; c0 < cout_p; c0 += 16) {
-            float v[16];
-            tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);  // all lanes take part
-            if (!inside) continue;
-            if (MODE == 1) {
-                float *o = static_cast<float *>(out) + vo * cout_p + c0;
+        for (int oz = 0; oz < OZ; oz++) {
+            const int z = z0 + oz;
+            if (z >= dm.D) break;  // uniform over the CTA
+            const size_t vo = (size_t)b * vol + ((size_t)z * dm.H + vy) * dm.W + vx;
+            for (int c0 = 0; c0 < cout_p; c0 += 16) {
+                float v[16];
+                tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(oz * TMEM_HALF + c0), v);  // all lanes
+                if (!inside) continue;
+                if (MODE == 1) {
+                    float *o = static_cast<float *>(out) + vo * cout_p + c0;
 #pragma unroll
-                for (int i = 0; i < 16; i += 4)
-                    *reinterpret_cast<float4 *>(o + i) =
-                        make_float4(v[i] + bias[c0 + i], v[i + 1] + bias[c0 + i + 1], v[i + 2] + bias[c0 + i + 2],
-                                    v[i + 3] + bias[c0 + i + 3]);
-            } else {
-                __align__(16) __nv_bfloat162 h[8];
-                if (MODE == 0) {
-#pragma unroll
-                    for (int i = 0; i < 8; i++)
-                        h[i] = __floats2bfloat162_rn(fmaxf(v[2 * i] + bias[c0 + 2 * i], 0.f),
-                                                     fmaxf(v[2 * i + 1] + bias[c0 + 2 * i + 1], 0.f));
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4 *>(o + i) =
+                            make_float4(v[i] + bias[c0 + i], v[i + 1] + bias[c0 + i + 1], v[i + 2] + bias[c0 + i + 2],
+                                        v[i + 3] + bias[c0 + i + 3]);
                 } else {
-                    __align__(16) __nv_bfloat162 g[8];
-                    const uint4 *gp = reinterpret_cast<const uint4 *>(gate + vo * cout_p + c0);
-                    reinterpret_cast<uint4 *>(g)[0] = gp[0];
-                    reinterpret_cast<uint4 *>(g)[1] = gp[1];
+                    __align__(16) __nv_bfloat162 h[8];
+                    if (MODE == 0) {
 #pragma unroll
-                    for (int i = 0; i < 8; i++)
-                        h[i] = __floats2bfloat162_rn(__bfloat162float(g[i].x) > 0.f ? v[2 * i] : 0.f,
-                                                     __bfloat162float(g[i].y) > 0.f ? v[2 * i + 1] : 0.f);
+                        for (int i = 0; i < 8; i++)
+                            h[i] = __floats2bfloat162_rn(fmaxf(v[2 * i] + bias[c0 + 2 * i], 0.f),
+                                                         fmaxf(v[2 * i + 1] + bias[c0 + 2 * i + 1], 0.f));
+                    } else {
+                        __align__(16) __nv_bfloat162 g[8];
+                        const uint4 *gp = reinterpret_cast<const uint4 *>(gate + vo * cout_p + c0);
+                        reinterpret_cast<uint4 *>(g)[0] = gp[0];
+                        reinterpret_cast<uint4 *>(g)[1] = gp[1];
+#pragma unroll
+                        for (int i = 0; i < 8; i++)
+                            h[i] = __floats2bfloat162_rn(__bfloat162float(g[i].x) > 0.f ? v[2 * i] : 0.f,
+                                                         __bfloat162float(g[i].y) > 0.f ? v[2 * i + 1] : 0.f);
+                    }
+                    uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + vo * cout_p + c0);
+                    o[0] = reinterpret_cast<uint4 *>(h)[0];
+                    o[1] = reinterpret_cast<uint4 *>(h)[1];
                 }
-                uint4 *o = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(out) + vo * cout_p + c0);
-                o[0] = reinterpret_cast<uint4 *>(h)[0];
-                o[1] = reinterpret_cast<uint4 *>(h)[1];
             }
         }
     }
@@ -495,7 +546,8 @@ cudaError_t launch(const __nv_bfloat16 *in, const __nv_bfloat16 *wpk, const floa
     cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int tiles = ((dm.W + TX - 1) / TX) * ((dm.H + TY - 1) / TY);
-    conv_tc_kernel<MODE><<<dim3(tiles, dm.D, dm.B), THREADS, smem, s>>>(in, wpk, bias, out, gate, dm, err);
+    conv_tc_kernel<MODE><<<dim3(tiles, (dm.D + OZ - 1) / OZ, dm.B), THREADS, smem, s>>>(in, wpk, bias, out, gate, dm,
+                                                                                     err);
     return cudaGetLastError();
 }
 
