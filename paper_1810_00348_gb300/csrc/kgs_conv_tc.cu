@@ -420,6 +420,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t bar[WG_BUF], done_bar;
     __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
     const int cout_p = dm.cout_p, cin_p = dm.cin_p, C8o = cout_p / 8, C8i = cin_p / 8;
     const WgLayout L = wg_layout(cin_p, cout_p);
     const uint32_t base = smem_u32(sm);
@@ -474,13 +475,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         cp_async_commit();
     };
 
-    bool ok = true;
+    // Thread 0 issues the MMAs and makes every wait on their completion; the
+    // other threads wait for it at CTA barriers rather than polling beside it
+    // in its warp.  s_fail records a wait that gave up (uniform after a barrier).
+    if (threadIdx.x == 0) s_fail = 0;
     for (int i = 0; i < WG_BUF - 1 && i < nt; i++) load_tile(i);
     for (int i = 0; i < nt; i++) {
         const int j = i + WG_BUF - 1;
         if (j < nt) {
             // tile j reuses the buffer of tile i - 1: its MMAs must have completed
-            if (i >= 1 && ok && !mbar_wait(smem_u32(&bar[(i - 1) % WG_BUF]), ((i - 1) / WG_BUF) & 1)) ok = false;
+            if (i >= 1) {
+                if (threadIdx.x == 0 && !s_fail && !mbar_wait(smem_u32(&bar[(i - 1) % WG_BUF]), ((i - 1) / WG_BUF) & 1))
+                    s_fail = 1;
+                __syncthreads();
+            }
             load_tile(j);
             cp_async_wait<WG_BUF - 1>();  // tile i has landed
         } else if (i + 1 < nt) {
@@ -492,7 +500,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        if (threadIdx.x == 0 && ok) {
+        if (threadIdx.x == 0 && !s_fail) {
             const uint32_t abuf = base + (uint32_t)(i % WG_BUF) * L.buf_bytes, hbuf = abuf + L.a_bytes;
 #pragma unroll 1
             for (int ks = 0; ks < TY / 2; ks++) {  // K = 16 voxels: tile rows 2ks, 2ks + 1
@@ -507,11 +515,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_commit(smem_u32(&bar[i % WG_BUF]));
         }
     }
-    if (threadIdx.x == 0) tc_commit(smem_u32(&done_bar));
-    const bool done = mbar_wait(smem_u32(&done_bar), 0);
+    if (threadIdx.x == 0) {
+        tc_commit(smem_u32(&done_bar));
+        if (!mbar_wait(smem_u32(&done_bar), 0)) s_fail = 1;
+    }
+    __syncthreads();
     tc_fence_after();
-    const bool good = __syncthreads_and(done && ok) != 0;  // uniform: the loads below are warp-collective
-    if (!good) {
+    if (s_fail) {  // uniform: the loads below are warp-collective
         if (threadIdx.x == 0) atomicExch(err, 1);
     } else {
         // row co = TMEM lane; columns kx * 128 + ci
