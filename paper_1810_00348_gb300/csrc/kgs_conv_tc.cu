@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     tc_fence_after();
 
+    int issued = NBUF - 1;  // last tap whose weight copy was issued (thread 0)
     if (threadIdx.x == 0) {
         // producer: tap t reuses the buffer of tap t - NBUF once its MMAs are done
         for (int t = NBUF; t < 27; t++) {
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 break;
             }
             issue_w(t);
+            issued = t;
         }
     } else if (threadIdx.x == 32) {
         // MMA issuer: per tap and channel pair, one MMA of 128 x N x 16 for
@@ -315,7 +317,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tmem = tmem_base;
     tc_fence_after();
     if (s_fail || last != 26) {
-        if (threadIdx.x == 0) atomicExch(err, 1);
+        if (threadIdx.x == 0) {
+            atomicExch(err, 1);
+            // weight copies issued but never consumed land before the CTA
+            // leaves (bounded; at most NBUF are outstanding, on distinct barriers)
+            for (int t = last + 1; t <= issued; t++) (void)mbar_wait(full(t), use(t));
+        }
     } else {
         const int row = warp * 32 + lane;
         const int vx = x0 + row % TX, vy = y0 + row / TX;
