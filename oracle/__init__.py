@@ -58,6 +58,8 @@ def _load():
         lib.kgso_moments.argtypes = [ctypes.c_void_p, _dbl_p, _dbl_p]
         lib.kgso_sweep.argtypes = [ctypes.c_void_p, ctypes.c_int, _dbl_p]
         lib.kgso_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.kgso_pass1_range.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dbl_p, _dbl_p, _dbl_p, _dbl_p]
+        lib.kgso_pass2_range.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dbl_p, _dbl_p]
         lib.kgso_parallel.restype = ctypes.c_int
         lib.kgso_ghost.restype = ctypes.c_double
         lib.kgso_ghost.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -123,6 +125,21 @@ class Oracle:
         if getattr(self, "_s", None):
             _load().kgso_destroy(self._s)
             self._s = None
+
+    def pass1_range(self, a0, a1):
+        """Sums of the first pass over velocities [a0, a1): rho, rho U, rho E and
+        the incoming wall fluxes, as one array [1 + 3 + 1 + 6][ncell]."""
+        out = np.zeros((11, self.ncell))
+        lib = _load()
+        lib.kgso_pass1_range(self._s, int(a0), int(a1), _ptr(out[0]), _ptr(out[1:4]), _ptr(out[4]), _ptr(out[5:11]))
+        return out
+
+    def pass2_range(self, a0, a1, U):
+        """q = 1/2 sum w c |c|^2 f over velocities [a0, a1), c = xi - U, as [3][ncell]."""
+        U = np.ascontiguousarray(U, dtype=np.float64).reshape(3, self.ncell)
+        out = np.zeros((3, self.ncell))
+        _load().kgso_pass2_range(self._s, int(a0), int(a1), _ptr(U), _ptr(out))
+        return out
 
     def iterate(self, n=1):
         r = None

@@ -516,6 +516,24 @@ static void pass2(const kgso_state *s, int a0, int a1, double *f, const double *
 
 void kgso_set_threads(kgso_state *s, int n) { s->threads = n > 1 ? n : 1; }
 
+/* The two passes of an outer iteration over one velocity range [a0, a1),
+ * added into caller-owned sums (rho [nc], mom [3][nc], rhoE [nc], F [6][nc];
+ * q [3][nc] about the given U [3][nc]): the unit of a velocity-space
+ * partition whose ranges are summed afterwards. */
+void kgso_pass1_range(const kgso_state *s, int a0, int a1, double *rho, double *mom, double *rhoE, double *F)
+{
+    double *f = (double *)calloc((size_t)s->ncell, sizeof(double));
+    pass1(s, a0, a1, f, rho, mom, rhoE, F);
+    free(f);
+}
+
+void kgso_pass2_range(const kgso_state *s, int a0, int a1, const double *U, double *q)
+{
+    double *f = (double *)calloc((size_t)s->ncell, sizeof(double));
+    pass2(s, a0, a1, f, U, q);
+    free(f);
+}
+
 int kgso_parallel(void)
 {
 #ifdef _OPENMP

@@ -64,6 +64,13 @@ double kgso_iterate(kgso_state *s);
 void kgso_set_threads(kgso_state *s, int n);
 int kgso_parallel(void);
 
+/* One outer iteration's two passes over velocities [a0, a1) only, added into
+ * caller-owned sums: rho [nc], mom [3][nc], rhoE [nc], wall fluxes F [6][nc];
+ * then q [3][nc] about U [3][nc] (Eq. (5)).  A velocity-space partition sums
+ * these over its ranges (the paper's MPI_Allreduce). */
+void kgso_pass1_range(const kgso_state *s, int a0, int a1, double *rho, double *mom, double *rhoE, double *F);
+void kgso_pass2_range(const kgso_state *s, int a0, int a1, const double *U, double *q);
+
 void kgso_get_macros(const kgso_state *s, double *out);    /* [8][ncell] */
 void kgso_get_rho_w(const kgso_state *s, double *out);     /* [6][ncell] */
 void kgso_set_rho_w(kgso_state *s, const double *in);      /* [6][ncell] */
