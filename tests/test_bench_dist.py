@@ -34,7 +34,7 @@ def test_two_ranks_agree_on_the_slowest_step():
     import torch.multiprocessing as mp
 
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)

@@ -57,7 +57,7 @@ def test_two_ranks_reduce_the_velocity_partition():
     import torch.multiprocessing as mp
 
     world = 2
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         res = mgr.dict()
         mp.spawn(_worker, args=(world, _free_port(), res), nprocs=world, join=True)
         res = dict(res)
