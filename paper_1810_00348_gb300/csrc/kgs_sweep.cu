@@ -68,7 +68,17 @@ __device__ __forceinline__ float rcp_approx(float x)
 // log2(e) factor already folded into the coefficient C_NEXP.
 __device__ __forceinline__ double eq_exp(double x) { return exp(x); }
 __device__ __forceinline__ float eq_exp(float x) { return ex2_approx(x); }
-__device__ __forceinline__ double implicit_div(double num, double den) { return num / den; }
+// FP64: the reciprocal of the denominator from the hardware approximation
+// refined by two Newton-Raphson steps r <- r + r (1 - den r) (quadratic
+// convergence, about 1 ulp), then one product; den = 1/tau + sum a_d > 0.
+__device__ __forceinline__ double implicit_div(double num, double den)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(den));
+    r = fma(r, fma(-den, r, 1.0), r);
+    r = fma(r, fma(-den, r, 1.0), r);
+    return num * r;
+}
 __device__ __forceinline__ float implicit_div(float num, float den) { return num * rcp_approx(den); }
 
 __host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
