@@ -564,27 +564,25 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 const int vend = min(vbeg + VG / 2, nvg);
                 // fold the line sums P_a (x-line of the tensor-product grid ending at
                 // velocity ve-1) with the line's c_y, c_z and w_y w_z
-                // The low parts of c = xi - U^n (float pairs) matter only in FP32:
-                // in FP64 the rounding of c is far below the path's tolerance, so
-                // the corrections below are compiled for the FP32 path only.
-                constexpr bool CORR = sizeof(Real) == 4;
-                auto fold = [&](Real P0, Real P1, Real P2, Real P3, int ve) {
-                    const Real *e = vt + (ve - 1) * VT;
-                    const Real W = e[3];
-                    const Real q0 = W * P0, q1 = W * P1, q2 = W * P2;
-                    S[P_S0].add(q0);
-                    S[P_S1X].add(q1);
-                    S[P_S2XX].add(q2);
-                    if constexpr (CORR) {
+                if constexpr (sizeof(Real) == 4) {
+                    // fold the line sums P_a (x-line of the tensor-product grid ending at
+                    // velocity ve-1) with the line's c_y, c_z and w_y w_z
+                    auto fold = [&](Real P0, Real P1, Real P2, Real P3, int ve) {
+                        const Real *e = vt + (ve - 1) * VT;
                         Real cy, cyl, cz, czl;
                         two_diff(e[1], uy, cy, cyl);
                         two_diff(e[2], uz, cz, czl);
                         cyl += e[4];
                         czl += e[5];
+                        const Real W = e[3];
+                        const Real q0 = W * P0, q1 = W * P1, q2 = W * P2;
                         const Real r2 = fma(cy, cy, cz * cz);
                         const Real r2l = Real(2) * fma(cy, cyl, cz * czl);
+                        S[P_S0].add(q0);
+                        S[P_S1X].add(q1);
                         S[P_S1Y].add(fma(cy, q0, cyl * q0));
                         S[P_S1Z].add(fma(cz, q0, czl * q0));
+                        S[P_S2XX].add(q2);
                         S[P_S2YY].add(fma(cy, cy, Real(2) * cy * cyl) * q0);
                         S[P_S2ZZ].add(fma(cz, cz, Real(2) * cz * czl) * q0);
                         S[P_S2XY].add(fma(cy, q1, cyl * q1));
@@ -594,11 +592,86 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                         const Real e2 = fma(r2, q0, fma(r2l, q0, q2));
                         S[P_S3Y].add(fma(cy, e2, cyl * e2));
                         S[P_S3Z].add(fma(cz, e2, czl * e2));
+                        // incoming flux w |xi_d| f towards the wall ahead
+                        if (wx) S[P_FX].add(sgnx * fma(ux, q0, q1));
+                        if (wy) S[P_FY].add(fabs(e[1]) * q0);
+                        if (wz) S[P_FZ].add(fabs(e[2]) * q0);
+                    };
+                    if constexpr (LINE > 0) {
+                        // Every x-line has LINE nodes and the thread's range holds whole
+                        // lines: the c_x pairs and w_x of the LINE nodes stay in registers.
+                        Real cxr[LINE], cxlr[LINE], wxr[LINE];
+    #pragma unroll
+                        for (int ix = 0; ix < LINE; ix++) {
+                            Real hi, lo;
+                            two_diff(xn[ix * 2], ux, hi, lo);
+                            cxr[ix] = hi;
+                            cxlr[ix] = lo + xn[ix * 2 + 1];
+                            wxr[ix] = vt[(vbeg + ix) * VT];
+                        }
+                        for (int v = vbeg; v < vend; v += LINE) {
+                            Real P0 = 0, P1 = 0, P2 = 0, P3 = 0, C1 = 0, C2 = 0, C3 = 0;
+    #pragma unroll
+                            for (int ix = 0; ix < LINE; ix++) {
+                                const Real f = sp[v + ix];
+                                const Real cx = cxr[ix];
+                                const Real t0 = wxr[ix] * f;
+                                const Real t1 = t0 * cx;
+                                const Real t2 = t1 * cx;
+                                P0 += t0;
+                                P1 += t1;
+                                P2 += t2;
+                                P3 = fma(t2, cx, P3);
+                                C1 = fma(t0, cxlr[ix], C1);
+                                C2 = fma(t1, cxlr[ix], C2);
+                                C3 = fma(t2, cxlr[ix], C3);
+                            }
+                            // first-order corrections for the low part of c_x
+                            fold(P0, P1 + C1, fma(Real(2), C2, P2), fma(Real(3), C3, P3), v + LINE);
+                        }
                     } else {
+                        const Real *cxhc = cxh + cl * cxs, *cxlc = cxl + cl * cxs;
+                        int v = vbeg;
+                        while (v < vend) {
+                            // one x-line segment [v, ve): velocities with the same (xi_y, xi_z)
+                            const int ix0 = (v0 + v) % nxo;
+                            const int ve = min(vend, v + (nxo - ix0));
+                            Real P0 = 0, P1 = 0, P2 = 0, P3 = 0, C1 = 0, C2 = 0, C3 = 0;
+    #pragma unroll 4
+                            for (int vv = v; vv < ve; vv++) {
+                                const int ix = ix0 + (vv - v);
+                                const Real f = sp[vv];
+                                const Real cx = cxhc[ix], cxlo = cxlc[ix];
+                                const Real t0 = vt[vv * VT] * f;
+                                const Real t1 = t0 * cx;
+                                const Real t2 = t1 * cx;
+                                P0 += t0;
+                                P1 += t1;
+                                P2 += t2;
+                                P3 = fma(t2, cx, P3);
+                                C1 = fma(t0, cxlo, C1);
+                                C2 = fma(t1, cxlo, C2);
+                                C3 = fma(t2, cxlo, C3);
+                            }
+                            fold(P0, P1 + C1, fma(Real(2), C2, P2), fma(Real(3), C3, P3), ve);
+                            v = ve;
+                        }
+                    }
+                } else {
+                    // FP64: the rounding of c = xi - U^n is far below the path's
+                    // tolerance, so the float-pair corrections of the FP32 path are
+                    // left out (fewer operations and registers).
+                    auto fold = [&](Real P0, Real P1, Real P2, Real P3, int ve) {
+                        const Real *e = vt + (ve - 1) * VT;
                         const Real cy = e[1] - uy, cz = e[2] - uz;
+                        const Real W = e[3];
+                        const Real q0 = W * P0, q1 = W * P1, q2 = W * P2;
                         const Real r2 = fma(cy, cy, cz * cz);
+                        S[P_S0].add(q0);
+                        S[P_S1X].add(q1);
                         S[P_S1Y].add(cy * q0);
                         S[P_S1Z].add(cz * q0);
+                        S[P_S2XX].add(q2);
                         S[P_S2YY].add(cy * cy * q0);
                         S[P_S2ZZ].add(cz * cz * q0);
                         S[P_S2XY].add(cy * q1);
@@ -608,85 +681,56 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                         const Real e2 = fma(r2, q0, q2);
                         S[P_S3Y].add(cy * e2);
                         S[P_S3Z].add(cz * e2);
-                    }
-                    // incoming flux w |xi_d| f towards the wall ahead
-                    if (wx) S[P_FX].add(sgnx * fma(ux, q0, q1));
-                    if (wy) S[P_FY].add(fabs(e[1]) * q0);
-                    if (wz) S[P_FZ].add(fabs(e[2]) * q0);
-                };
-                if constexpr (LINE > 0) {
-                    // Every x-line has LINE nodes and the thread's range holds whole
-                    // lines: the c_x pairs and w_x of the LINE nodes stay in registers.
-                    Real cxr[LINE], cxlr[LINE], wxr[LINE];
-#pragma unroll
-                    for (int ix = 0; ix < LINE; ix++) {
-                        if constexpr (CORR) {
-                            Real hi, lo;
-                            two_diff(xn[ix * 2], ux, hi, lo);
-                            cxr[ix] = hi;
-                            cxlr[ix] = lo + xn[ix * 2 + 1];
-                        } else {
-                            cxr[ix] = xn[ix * 2] - ux;
-                        }
-                        wxr[ix] = vt[(vbeg + ix) * VT];
-                    }
-                    for (int v = vbeg; v < vend; v += LINE) {
-                        Real P0 = 0, P1 = 0, P2 = 0, P3 = 0, C1 = 0, C2 = 0, C3 = 0;
-#pragma unroll
+                        if (wx) S[P_FX].add(sgnx * fma(ux, q0, q1));
+                        if (wy) S[P_FY].add(fabs(e[1]) * q0);
+                        if (wz) S[P_FZ].add(fabs(e[2]) * q0);
+                    };
+                    if constexpr (LINE > 0) {
+                        Real cxr[LINE], wxr[LINE];
+    #pragma unroll
                         for (int ix = 0; ix < LINE; ix++) {
-                            const Real f = sp[v + ix];
-                            const Real cx = cxr[ix];
-                            const Real t0 = wxr[ix] * f;
-                            const Real t1 = t0 * cx;
-                            const Real t2 = t1 * cx;
-                            P0 += t0;
-                            P1 += t1;
-                            P2 += t2;
-                            P3 = fma(t2, cx, P3);
-                            if constexpr (CORR) {
-                                C1 = fma(t0, cxlr[ix], C1);
-                                C2 = fma(t1, cxlr[ix], C2);
-                                C3 = fma(t2, cxlr[ix], C3);
-                            }
+                            cxr[ix] = xn[ix * 2] - ux;
+                            wxr[ix] = vt[(vbeg + ix) * VT];
                         }
-                        // first-order corrections for the low part of c_x
-                        if constexpr (CORR)
-                            fold(P0, P1 + C1, fma(Real(2), C2, P2), fma(Real(3), C3, P3), v + LINE);
-                        else
+                        for (int v = vbeg; v < vend; v += LINE) {
+                            Real P0 = 0, P1 = 0, P2 = 0, P3 = 0;
+    #pragma unroll
+                            for (int ix = 0; ix < LINE; ix++) {
+                                const Real f = sp[v + ix];
+                                const Real cx = cxr[ix];
+                                const Real t0 = wxr[ix] * f;
+                                const Real t1 = t0 * cx;
+                                const Real t2 = t1 * cx;
+                                P0 += t0;
+                                P1 += t1;
+                                P2 += t2;
+                                P3 = fma(t2, cx, P3);
+                            }
                             fold(P0, P1, P2, P3, v + LINE);
-                    }
-                } else {
-                    const Real *cxhc = cxh + cl * cxs, *cxlc = cxl + cl * cxs;
-                    int v = vbeg;
-                    while (v < vend) {
-                        // one x-line segment [v, ve): velocities with the same (xi_y, xi_z)
-                        const int ix0 = (v0 + v) % nxo;
-                        const int ve = min(vend, v + (nxo - ix0));
-                        Real P0 = 0, P1 = 0, P2 = 0, P3 = 0, C1 = 0, C2 = 0, C3 = 0;
-#pragma unroll 4
-                        for (int vv = v; vv < ve; vv++) {
-                            const int ix = ix0 + (vv - v);
-                            const Real f = sp[vv];
-                            const Real cx = cxhc[ix];
-                            const Real t0 = vt[vv * VT] * f;
-                            const Real t1 = t0 * cx;
-                            const Real t2 = t1 * cx;
-                            P0 += t0;
-                            P1 += t1;
-                            P2 += t2;
-                            P3 = fma(t2, cx, P3);
-                            if constexpr (CORR) {
-                                const Real cxlo = cxlc[ix];
-                                C1 = fma(t0, cxlo, C1);
-                                C2 = fma(t1, cxlo, C2);
-                                C3 = fma(t2, cxlo, C3);
-                            }
                         }
-                        if constexpr (CORR)
-                            fold(P0, P1 + C1, fma(Real(2), C2, P2), fma(Real(3), C3, P3), ve);
-                        else
+                    } else {
+                        const Real *cxhc = cxh + cl * cxs;
+                        int v = vbeg;
+                        while (v < vend) {
+                            const int ix0 = (v0 + v) % nxo;
+                            const int ve = min(vend, v + (nxo - ix0));
+                            Real P0 = 0, P1 = 0, P2 = 0, P3 = 0;
+    #pragma unroll 4
+                            for (int vv = v; vv < ve; vv++) {
+                                const int ix = ix0 + (vv - v);
+                                const Real f = sp[vv];
+                                const Real cx = cxhc[ix];
+                                const Real t0 = vt[vv * VT] * f;
+                                const Real t1 = t0 * cx;
+                                const Real t2 = t1 * cx;
+                                P0 += t0;
+                                P1 += t1;
+                                P2 += t2;
+                                P3 = fma(t2, cx, P3);
+                            }
                             fold(P0, P1, P2, P3, ve);
-                        v = ve;
+                            v = ve;
+                        }
                     }
                 }
             }
