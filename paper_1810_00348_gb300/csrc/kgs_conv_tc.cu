@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mbar_arrive(smem_u32(&plane_full[1]));
     }
-    __syncthreads();  // the verdict in s_fail / s_last is uniform after it
+    __syncthreads();  // the outcome in s_fail / s_last is uniform after it
     const int last = s_last;
     const uint32_t tmem = tmem_base;
     tc_fence_after();
