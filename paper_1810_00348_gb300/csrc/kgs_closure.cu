@@ -104,11 +104,15 @@ struct FFSum {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// Closure of one outer iteration for CLOSE_CELLS cells per block: thread
-// (cell, slot q) sums partial q of its cell over all velocity groups in group
-// order (a warp reads the contiguous partials of two cells per group; 16
-// threads per cell keep many loads in flight), then one thread per cell turns
-// the sums into the macroscopic fields and wall densities.
+// Closure of one outer iteration for CLOSE_CELLS cells per block.  The sums
+// come first: the first 13 warps hold (cell, moment slot) pairs, each thread
+// summing one slot of one cell over all velocity groups in group order (a
+// cell's slots are contiguous, so a warp's loads cover a few 128-byte rows);
+// the last 3 warps hold (cell, axis) pairs for the incoming wall fluxes,
+// which split by the side of the group's octant.  The two kinds never share
+// a warp, so neither takes the other's branch.  Then one thread per cell
+// turns the sums into the macroscopic fields and wall densities.
+static_assert(CLOSE_CELLS * 13 % 32 == 0 && CLOSE_CELLS * 3 % 32 == 0, "slot warps must not mix");
 template <typename Real>
 __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseArgs a)
 {
@@ -116,29 +120,34 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
     __shared__ double sS[CLOSE_CELLS][NS];
     const size_t ncell = a.ncell;
     {
-    const int cl = threadIdx.x / NPART, q = threadIdx.x % NPART;
+    const int t = threadIdx.x;
+    const bool flux = t >= CLOSE_CELLS * P_FX;  // uniform per warp
+    const int cl = flux ? (t - CLOSE_CELLS * P_FX) / 3 : t / P_FX;
+    const int axis = flux ? (t - CLOSE_CELLS * P_FX) % 3 : 0;  // flux slots: incoming flux along x, y, z
+    const int q = flux ? P_FX + axis : t % P_FX;
     const size_t c = (size_t)blockIdx.x * CLOSE_CELLS + cl;
     const bool live = c < ncell && !(a.solid && a.solid[c]);
     if (live) {
-        const int axis = q - P_FX;  // flux slots: incoming flux along x, y, z
         double sum, f_minus, f_plus;
         if (sizeof(Real) == 8) {
             sum = f_minus = f_plus = 0.0;
             const double *pp = static_cast<const double *>(a.part) + c * NPART + q;
+            if (!flux) {
 #pragma unroll 4
-            for (int g = 0; g < a.n_vg; g++) {
-                const double v = pp[(size_t)g * ncell * NPART];
-                if (q < P_FX)
-                    sum += v;
-                else if ((a.vg_oct[g] >> axis) & 1)  // the wall ahead of the group's octant
-                    f_plus += v;
-                else
-                    f_minus += v;
+                for (int g = 0; g < a.n_vg; g++) sum += pp[(size_t)g * ncell * NPART];
+            } else {
+#pragma unroll 4
+                for (int g = 0; g < a.n_vg; g++) {
+                    const double v = pp[(size_t)g * ncell * NPART];
+                    const bool ahead = (a.vg_oct[g] >> axis) & 1;  // the wall ahead of the group's octant
+                    f_plus += ahead ? v : 0.0;                       // adding an exact zero changes nothing
+                    f_minus += ahead ? 0.0 : v;
+                }
             }
         } else {
             // FP32 partials are compensated pairs (value = x - y); they are
             // summed as float-float numbers (hi + lo, hi updated by an error-
-            // free two-sum) on the FP32 pipe and widened once at the end
+            // free two-sum) on the FP32 pipe and widened once at the end.
             // The loads go in batches of CB groups into registers, the next
             // batch issued before the current one is summed, so that up to
             // 2 CB loads per thread are in flight.
@@ -155,14 +164,21 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
             load(cur, 0);
             for (int g0 = 0; g0 < n_vg; g0 += CB) {
                 if (g0 + CB < n_vg) load(nxt, g0 + CB);
+                if (!flux) {
 #pragma unroll
-                for (int k = 0; k < CB; k++) {
-                    const int g = g0 + k;
-                    if (g < n_vg) {
-                        if (q >= P_FX && ((a.vg_oct[g] >> axis) & 1))
-                            acc1.add(cur[k].x, cur[k].y);
-                        else
-                            acc0.add(cur[k].x, cur[k].y);
+                    for (int k = 0; k < CB; k++)
+                        if (g0 + k < n_vg) acc0.add(cur[k].x, cur[k].y);
+                } else {
+                    // both sides take every group, one of them an exact zero
+                    // pair, which leaves a float-float sum unchanged
+#pragma unroll
+                    for (int k = 0; k < CB; k++) {
+                        const int g = g0 + k;
+                        if (g < n_vg) {
+                            const bool ahead = (a.vg_oct[g] >> axis) & 1;
+                            acc1.add(ahead ? cur[k].x : 0.f, ahead ? cur[k].y : 0.f);
+                            acc0.add(ahead ? 0.f : cur[k].x, ahead ? 0.f : cur[k].y);
+                        }
                     }
                 }
 #pragma unroll
@@ -171,7 +187,7 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
             sum = f_minus = acc0.value();
             f_plus = acc1.value();
         }
-        if (q < P_FX) {
+        if (!flux) {
             sS[cl][q] = sum;
         } else {
             sS[cl][13 + 2 * axis] = f_minus;
@@ -232,8 +248,10 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
         for (int v = 0; v < 8; v++) a.mac_new[v * ncell + c] = 0.0;
         for (int s = 0; s < 6; s++) a.rho_w_new[s * ncell + c] = 0.0;
     }
-    // fixed-order sum of the block's cell masses (lanes 0..15)
-    for (int off = CLOSE_CELLS / 2; off > 0; off >>= 1) mass += __shfl_down_sync(0xffffu, mass, off, CLOSE_CELLS);
+    // fixed-order sum of the block's cell masses (lanes 0 .. CLOSE_CELLS-1)
+    static_assert(CLOSE_CELLS <= 32, "one warp per block's cells");
+    constexpr unsigned mask = CLOSE_CELLS == 32 ? 0xffffffffu : (1u << CLOSE_CELLS) - 1u;
+    for (int off = CLOSE_CELLS / 2; off > 0; off >>= 1) mass += __shfl_down_sync(mask, mass, off, CLOSE_CELLS);
     if (threadIdx.x == 0) a.blk_mass[blockIdx.x] = mass;
 }
 

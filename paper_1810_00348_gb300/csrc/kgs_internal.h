@@ -165,7 +165,7 @@ cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, 
                         double mu_ref, double omega, double Pr, void *coef, cudaStream_t s);
 // Cells per block of the closure kernel; blk_mass holds close_blocks(ncell)
 // values.
-constexpr int CLOSE_CELLS = 16;
+constexpr int CLOSE_CELLS = 32;
 inline size_t close_blocks(size_t ncell) { return (ncell + CLOSE_CELLS - 1) / CLOSE_CELLS; }
 cudaError_t launch_close(const CloseArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_mass(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale,
