@@ -189,8 +189,9 @@ def run_reference(args, world, rank):
         vals.append(time_oracle_sample()["value"])
     v = statistics.median(vals)
     cb["value"] = v
+    sample_pp = float(N_CELL ** 3 * 8 ** 3)  # phase points of one sampled step
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "phase-point updates/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample_pp / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD + " (oracle sample: 8^3 velocities)"},
             "cpu_baseline": cb,
