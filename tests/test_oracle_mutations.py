@@ -54,3 +54,7 @@ def test_pins_fail_on_a_planted_bug(tmp_path, label, old, new):
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, "no pin caught: %s\n%s" % (label, r.stdout[-2000:])
+    # a pin's assertion rejected the mutant, not an exception raised by it
+    for exc in ("IndexError", "ValueError", "TypeError", "NameError", "AttributeError", "OSError"):
+        assert exc not in r.stdout, r.stdout[-2000:]
+    assert "assert" in r.stdout, r.stdout[-2000:]
