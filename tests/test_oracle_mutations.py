@@ -26,6 +26,10 @@ MUTATIONS = [
      "cc[d] = xi[d] - U[(size_t)d * nc + c];", "cc[d] = xi[d];"),
     ("relaxation rate scaled",
      "    return p / mu;", "    return 2.0 * p / mu;"),
+    ("viscosity law with T^(omega - 1) in place of T^omega",
+     "double mu = s->mu_ref * pow(T, s->p.omega);", "double mu = s->mu_ref * pow(T, s->p.omega - 1.0);"),
+    ("pressure in the relaxation time without the gas constant",
+     "double p = rho * R_GAS * T;\n    return p / mu;", "double p = rho * T;\n    return p / mu;"),
     ("incoming wall flux without the quadrature weight",
      "return xn < 0.0 ? w * (-xn) * f : 0.0;", "return xn < 0.0 ? (-xn) * f : 0.0;"),
     ("temperature without the kinetic energy subtracted",

@@ -113,6 +113,52 @@ def test_mu_ref_argon():
     np.testing.assert_allclose(Oracle(p).mu_ref(), 0.7310329, rtol=1e-6)
 
 
+def _sheared_column(rho0, T0, Kn, shear):
+    """A column of 32 cells across a unit gap in y whose cells are 1e6 wide in
+    x and z (the side walls then reach the middle cells only through upwind
+    weights of order 1e-7), with the lagged state rho0, T0, q = 0 and the
+    weak shear U_x = shear (y - 1/2).  The walls at y = 0 and y = 1 move with
+    the gas next to them, at T0."""
+    ny = 32
+    p = inputs.cavity([1, ny, 1], 28, L_v=6.5, Kn=Kn, T_w=T0)
+    p.dx = np.array([1e6])
+    p.dz = np.array([1e6])
+    p.U_w[2] = [-0.5 * shear, 0.0, 0.0]
+    p.U_w[3] = [0.5 * shear, 0.0, 0.0]
+    y = (np.arange(ny) + 0.5) / ny
+    mac = np.zeros((8, 1, ny, 1))
+    mac[0] = rho0
+    mac[4] = T0
+    mac[1, 0, :, 0] = shear * (y - 0.5)
+    return p, mac
+
+
+@pytest.mark.parametrize("rho0,T0", [(1.0, 1.0), (2.0, 1.0), (1.0, 2.0), (0.5, 1.5)])
+def test_relaxation_time_gives_the_viscosity(rho0, T0):
+    """tau = mu / p with mu = mu_ref T^omega and p = rho R T (Section 2.1,
+    Eq. (10)), checked through a consequence: the shear stress of a weakly
+    sheared gas.  Away from the walls the first-order upwind solution of an
+    equilibrium that is affine in y is exactly f = f^S - tau xi_y df^S/dy (the
+    Chapman-Enskog solution: the upwind difference of an affine profile is
+    its exact derivative), whose shear stress is P_xy = -p tau dU_x/dy.  So
+    the swept field of the middle cells must carry the viscosity
+    mu(T) = mu_ref T^omega: independent of the density (the classic kinetic
+    theory result), growing as T^omega with the temperature.  mu_ref is pinned
+    by the hard-sphere relation above."""
+    shear, Kn = 0.02, 0.004
+    p, mac = _sheared_column(rho0, T0, Kn, shear)
+    o = Oracle(p, mac)
+    xi, w = brute.velocities(p)
+    ny = p.ny
+    f = np.array([o.sweep(a).reshape(-1) for a in range(p.nvel)])  # [nvel][ny]
+    for j in (ny // 2 - 1, ny // 2):
+        U = mac[1:4, 0, j, 0]
+        c = xi - U[None, :]
+        Pxy = np.sum(w * c[:, 0] * c[:, 1] * f[:, j])
+        mu = o.mu_ref() * T0 ** p.omega
+        assert abs(-Pxy / (mu * shear) - 1.0) < 1e-5, (rho0, T0, -Pxy / shear, mu)
+
+
 # ---------------------------------------------------------------------------
 # Section 3.4 boundary values
 
