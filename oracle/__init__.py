@@ -32,6 +32,7 @@ class _Problem(ctypes.Structure):
         ("T_solid", ctypes.c_double),
         ("wall_mode", ctypes.c_int),
         ("mass_rescale", ctypes.c_int),
+        ("q_lagged", ctypes.c_int),
     ]
 
 
@@ -109,6 +110,7 @@ class Oracle:
         P.T_solid = prob.T_solid
         P.wall_mode = int(prob.wall_mode)
         P.mass_rescale = int(prob.mass_rescale)
+        P.q_lagged = int(getattr(prob, "q_lagged", 0))
         self._P = P
         m0 = None
         if macros0 is not None:

@@ -589,9 +589,18 @@ double kgso_iterate(kgso_state *s)
     }
     /* Pass 2: the heat flux of Eq. (5) needs the new U, so every velocity is
      * swept again (the sweep is deterministic) and q = 1/2 sum w c c^2 f is
-     * accumulated with c = xi - U^{n+1}. */
+     * accumulated with c = xi - U^{n+1}.  Option: the peculiar velocity taken
+     * about the lagged U^n instead (Algorithm 3 accumulates its eight moments
+     * in one pass, before the new U is known); the two agree at the fixed
+     * point. */
+    const double *Uq = U;
+    double *Ulag = NULL;
+    if (s->p.q_lagged) {
+        Ulag = copy_array(s->mac + nc, 3 * nc);
+        Uq = Ulag;
+    }
     if (s->threads <= 1) {
-        pass2(s, 0, s->nvel, s->f, U, q);
+        pass2(s, 0, s->nvel, s->f, Uq, q);
     } else {
         const int T = s->threads;
         double *f_t = (double *)calloc((size_t)T * nc, sizeof(double));
@@ -601,12 +610,13 @@ double kgso_iterate(kgso_state *s)
 #endif
         for (int t = 0; t < T; t++)
             pass2(s, (int)((long long)s->nvel * t / T), (int)((long long)s->nvel * (t + 1) / T), f_t + (size_t)t * nc,
-                  U, acc + (size_t)t * 3 * nc);
+                  Uq, acc + (size_t)t * 3 * nc);
         for (int t = 0; t < T; t++)
             for (size_t i = 0; i < (size_t)3 * nc; i++) q[i] += acc[(size_t)t * 3 * nc + i];
         free(acc);
         free(f_t);
     }
+    free(Ulag);
 
     int bad = 0;
     for (int c = 0; c < nc; c++) {

@@ -42,6 +42,7 @@ typedef struct {
     double T_solid;                      /* temperature of solid-cell surfaces     */
     int wall_mode;                       /* KGSO_WALL_DISCRETE / KGSO_WALL_ANALYTIC */
     int mass_rescale;                    /* 1: keep total mass fixed (Section 3.4) */
+    int q_lagged;                        /* 1: heat flux about the lagged U^n      */
 } kgso_problem;
 
 typedef struct kgso_state kgso_state;

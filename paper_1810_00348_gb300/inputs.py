@@ -60,6 +60,7 @@ class Problem:
     T_solid: float = 1.0
     wall_mode: int = WALL_DISCRETE
     mass_rescale: int = 1
+    q_lagged: int = 0                       # 1: heat flux about the lagged U^n (Algorithm 3's moments)
     name: str = ""
 
     @property

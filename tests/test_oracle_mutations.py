@@ -30,6 +30,8 @@ MUTATIONS = [
      "double mu = s->mu_ref * pow(T, s->p.omega);", "double mu = s->mu_ref * pow(T, s->p.omega - 1.0);"),
     ("pressure in the relaxation time without the gas constant",
      "double p = rho * R_GAS * T;\n    return p / mu;", "double p = rho * T;\n    return p / mu;"),
+    ("lagged heat flux taken about the new velocity",
+     "        Uq = Ulag;", "        Uq = U;"),
     ("incoming wall flux without the quadrature weight",
      "return xn < 0.0 ? w * (-xn) * f : 0.0;", "return xn < 0.0 ? (-xn) * f : 0.0;"),
     ("temperature without the kinetic energy subtracted",

@@ -462,3 +462,46 @@ def test_concurrent_velocity_ranges_match_the_serial_loop():
     err = field_errors(ranged.macros(), serial.macros())
     assert max(err.values()) < 1e-12, err
     assert np.max(np.abs(ranged.rho_w() - serial.rho_w())) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 3's heat flux about the lagged velocity (option)
+
+def test_lagged_heat_flux_is_the_moment_about_the_old_velocity():
+    """With q_lagged the heat flux of step n+1 is 1/2 sum w (xi - U^n)
+    |xi - U^n|^2 f^{n+1}, the lagged U^n of the input state (Algorithm 3
+    accumulates its moments in one pass, before the new U is known); rho, U
+    and T are those of the exact form.  The reference sums the oracle's swept
+    distribution with numpy."""
+    p = inputs.cavity([4, 3, 5], [6, 5, 7], L_v=3.5, lid=0.2, Kn=0.4, mass_rescale=0)
+    mac = inputs.random_macros(p, 71)
+    exact = Oracle(p, mac)
+    p.q_lagged = 1
+    lag = Oracle(p, mac)
+    xi, w = brute.velocities(p)
+    f = np.array([lag.sweep(a).reshape(-1) for a in range(p.nvel)])  # [nvel][ncell]
+    exact.iterate()
+    lag.iterate()
+    m_e, m_l = exact.macros().reshape(8, -1), lag.macros().reshape(8, -1)
+    np.testing.assert_allclose(m_l[:5], m_e[:5], rtol=1e-13, atol=1e-15)
+    U = mac.reshape(8, -1)[1:4]
+    c = xi[:, :, None] - U[None, :, :]  # [nvel][3][ncell]
+    c2 = np.sum(c * c, axis=1)
+    q_ref = 0.5 * np.einsum("a,adc,ac,ac->dc", w, c, c2, f)
+    np.testing.assert_allclose(m_l[5:8], q_ref, rtol=1e-12, atol=1e-14)
+    assert np.max(np.abs(m_l[5:8] - m_e[5:8])) > 1e-6  # the two forms differ away from the fixed point
+
+
+def test_lagged_heat_flux_has_the_same_fixed_point():
+    """At the fixed point U^{n+1} = U^n, so both heat-flux forms converge to
+    the same fields."""
+    out = []
+    for lagged in (0, 1):
+        p = inputs.cavity(4, 8, L_v=4.0, lid=0.2, Kn=0.5)
+        p.q_lagged = lagged
+        o = Oracle(p)
+        for _ in range(400):
+            if o.iterate() < 1e-13:
+                break
+        out.append(o.macros())
+    np.testing.assert_allclose(out[1], out[0], rtol=0, atol=1e-11)
