@@ -150,23 +150,27 @@ def rel_errors(got, ref):
     return err
 
 
-def time_oracle_sample(kgs=None):
-    """Oracle (plain serial FP64 C) on a bounded sample of the workload: the
+def time_oracle_sample(kgs=None, threads=1):
+    """Oracle (plain FP64 C) on a bounded sample of the workload: the
     64^3-cell cavity with an 8^3 velocity grid (one outer iteration, about 15 s
-    on one core).  Given the library, the GPU FP64 and mixed paths run the
-    same iteration and their errors against the oracle's result are reported."""
-    from oracle import Oracle
+    on one core).  threads > 1 runs the oracle's concurrent velocity ranges
+    on that many host threads (the same arithmetic, summed in range order).
+    Given the library, the GPU FP64 and mixed paths run the same iteration and
+    their errors against the oracle's result are reported."""
+    from oracle import Oracle, parallel_build
     from paper_1810_00348_gb300 import inputs
 
+    if threads > 1 and not parallel_build():
+        threads = 1
     prob = inputs.cavity(N_CELL, 8, Kn=KN, lid=LID)
-    o = Oracle(prob)
+    o = Oracle(prob, threads=threads)
     t0 = time.perf_counter()
     o.iterate()
     dt = time.perf_counter() - t0
     pp = prob.phase_points()
-    out = {"value": pp / dt, "unit": "phase-point updates/s", "cores": 1, "kind": "oracle",
+    out = {"value": pp / dt, "unit": "phase-point updates/s", "cores": threads, "kind": "oracle",
            "sample": "one outer iteration of the 64^3-cell cavity with an 8^3 velocity grid "
-                     "(%d phase points, %.1f s on one host core)" % (pp, dt)}
+                     "(%d phase points, %.1f s on %d host thread%s)" % (pp, dt, threads, "s" if threads > 1 else "")}
     if kgs is not None:
         ref = o.macros()
         out["gpu_error_vs_oracle"] = {}
@@ -181,12 +185,14 @@ def time_oracle_sample(kgs=None):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    # the oracle is plain serial CPU code with no warm-up effects: every step
-    # is a timed sample
-    cb = time_oracle_sample()
+    # the oracle is plain CPU code with no warm-up effects: every step is a
+    # timed sample, run on all host cores so that the whole run stays within
+    # a few minutes
+    cores = os.cpu_count() or 1
+    cb = time_oracle_sample(threads=cores)
     vals = [cb["value"]]
     for _ in range(max(args.steps - 1, 0)):
-        vals.append(time_oracle_sample()["value"])
+        vals.append(time_oracle_sample(threads=cores)["value"])
     v = statistics.median(vals)
     cb["value"] = v
     sample_pp = float(N_CELL ** 3 * 8 ** 3)  # phase points of one sampled step

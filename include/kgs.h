@@ -116,7 +116,16 @@ typedef struct {
  *                precision, 256 for KGS_MIXED, 128 for KGS_FP64), 128, or 256
  *                (KGS_MIXED only); block_z cells per sweep block along z
  *                (0 = default, 32).
- *   stream       cudaStream_t to launch on (NULL = legacy default stream). */
+ *   stream       cudaStream_t to launch on (NULL = legacy default stream).
+ *   q_lagged     0: heat flux of Eq. (5) about the new velocity U^{n+1}
+ *                (default).  1: about the lagged velocity U^n, the single-pass
+ *                form of Algorithm 3's eight moments; the two agree at the
+ *                fixed point.
+ *   vz_begin, vz_end  velocity-space partition: the context sweeps only the
+ *                velocity planes iz in [vz_begin, vz_end) (0, 0 = all).  Its
+ *                per-cell sums (kgs_sweep_sums) are then partial; the wall
+ *                normalisation and the initial wall densities still use the
+ *                whole velocity grid. */
 typedef struct {
     int precision;
     int wall_norm;
@@ -126,6 +135,8 @@ typedef struct {
     int v_per_cta;
     int block_z;
     void *stream;
+    int q_lagged;
+    int vz_begin, vz_end;
 } kgs_opts;
 
 /* Sizes and counters of a context. */
@@ -204,6 +215,31 @@ int kgs_info(kgs_ctx *ctx, kgs_info_t *out);
 int kgs_set_profiling(kgs_ctx *ctx, int enable);
 int kgs_profile(kgs_ctx *ctx, double *sweep_ms, long long *sweep_launches, long long *kernel_launches);
 
+/* ---- velocity-space partition ----
+ * Within an outer iteration the velocities are independent (Eq. (6) lags
+ * f^S, tau and rho_w), so the sweep splits over velocity ranges whose moment
+ * sums are added before the closure: the paper's MPI CPU twin sums its
+ * ranges with MPI_Allreduce (Section 5).  Each part is a context made with
+ * kgs_opts.vz_begin / vz_end on the same problem and state.
+ *
+ * kgs_sweep_sums: the coefficient, sweep and moment kernels of one outer
+ * iteration over this context's velocities, without the closure; writes the
+ * per-cell sums to sums_dev[19][nz][ny][nx] (device, FP64, caller-owned): the
+ * 13 sums about the lagged velocity U^n (as rounded to the sweep precision)
+ * -- S0, S1 x y z, S2 xx yy zz xy xz yz, S3 x y z, with S_a = sum w f c^a,
+ * c = xi - U^n and S3_i = sum w f c_i |c|^2 -- then the incoming flux onto
+ * the wall on each side -x, +x, -y, +y, -z, +z (Eq. (9)).  The state does not
+ * change.  Synchronises the context's stream.
+ *
+ * kgs_close_sums: the closure of the outer iteration from sums_dev (device,
+ * the element-wise sum of every part's kgs_sweep_sums, same layout):
+ * macroscopic fields of Eq. (5), wall densities of Eq. (9), mass rescale and
+ * residual as kgs_iterate; advances the state by one iteration.  *residual
+ * (may be NULL) receives the residual.  Returns KGS_OK, KGS_EDIVERGED,
+ * KGS_ECUDA. */
+int kgs_sweep_sums(kgs_ctx *ctx, double *sums_dev);
+int kgs_close_sums(kgs_ctx *ctx, const double *sums_dev, double *residual);
+
 void kgs_destroy(kgs_ctx *ctx);
 const char *kgs_strerror(int code);
 
@@ -226,6 +262,7 @@ typedef struct {
     kgs_bc bc;
     int wall_norm;            /* KGS_WALL_DISCRETE / KGS_WALL_ANALYTIC */
     int mass_rescale;
+    int q_lagged;             /* as kgs_opts.q_lagged */
 } kgs_problem;
 
 /* Sweep shape (velocities per thread block, block depth along z) of one
@@ -238,8 +275,8 @@ int kgs_autotune(const kgs_problem *prob, int precision, int *v_per_cta, int *bl
 /* Build a batch of n instances (inputs copied; each instance starts from the
  * uniform state like kgs_setup).  opts: precision, tol, max_iters, stream;
  * v_per_cta = block_z = 0 asks kgs_autotune for the shape of the largest
- * instance, which then applies to all; wall_norm and mass_rescale come from
- * each kgs_problem.  Errors as kgs_setup. */
+ * instance, which then applies to all; wall_norm, mass_rescale and q_lagged
+ * come from each kgs_problem.  Errors as kgs_setup. */
 int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_opts *opts);
 
 /* n_iters > 0: exactly n_iters outer iterations of every instance.
@@ -261,6 +298,25 @@ int kgs_batch_info(kgs_batch *b, int i, kgs_info_t *out);
 /* Summed device time (ms) of the persistent sweep launches, their number and
  * the number of kernel launches since the last call; resets the counters. */
 int kgs_batch_profile(kgs_batch *b, double *sweep_ms, long long *sweeps, long long *kernel_launches);
+
+/* Solve every instance to opts.tol as kgs_solve does one problem: a mixed
+ * batch iterates each instance in chunks of 5 until its residual reaches
+ * opts.tol or stops falling (the same rule as kgs_solve), and the instance
+ * then retires from the mixed work list; an FP64 batch continues every
+ * instance from its mixed state (macros, wall densities, mass target) until
+ * its residual is below opts.tol, retiring instances as they converge.  An
+ * instance may run at most opts.max_iters iterations in all (at least one in
+ * FP64).  opts.precision is ignored; v_per_cta / block_z shape the mixed
+ * batch (0: autotuned), the FP64 batch takes 128 velocities per thread block
+ * and opts.block_z (0: 32).  *out receives the FP64 batch holding the
+ * results (kgs_batch_moments, kgs_batch_info; destroy with
+ * kgs_batch_destroy).  iters_mixed[n], iters_fp64[n], residuals[n] (host,
+ * may be NULL): iterations per phase and final residual of each instance.
+ * Returns KGS_OK, KGS_NOTCONVERGED (some instance ended above tol; *out is
+ * still set), or the errors of kgs_batch_setup / kgs_batch_iterate (*out =
+ * NULL). */
+int kgs_batch_solve(kgs_batch **out, int n, const kgs_problem *probs, const kgs_opts *opts, int *iters_mixed,
+                    int *iters_fp64, double *residuals);
 
 /* Failure-detection controls (for tests): spin_limit = polls (about 100 ns
  * each) before a wait for an upwind block gives up (default 2e7, about 2 s);
@@ -363,12 +419,21 @@ int kgs_surrogate_apply(long long ncell, const double *up, const float *y, doubl
  * kgs_setup, from the state (macros_in [8][nz][ny][nx], rho_w_in
  * [6][nz][ny][nx], device, FP64) to (macros_out, rho_w_out, device, FP64,
  * caller-owned, distinct from the inputs), on `stream` (cudaStream_t, NULL =
- * legacy default stream) of the current device.  M0 > 0 rescales the total
- * mass to M0 (Section 3.4); M0 <= 0 skips the rescale.  precision and
- * wall_norm as in kgs_opts; the velocities per thread block and the block
- * depth take their defaults.  *residual (host, may be NULL) receives the
- * Section 4.1 residual of the step.  The call returns after the iteration has
- * completed on the GPU.
+ * legacy default stream) of the current device.  M0 > 0 multiplies the new
+ * density, heat flux and wall densities by one common factor so that the
+ * total mass (sum of density times cell volume over the fluid cells) equals
+ * M0; M0 <= 0 leaves them unscaled.  precision and wall_norm as in kgs_opts;
+ * the velocities per thread block and the block depth take their defaults.
+ * *residual (host, may be NULL) receives the step's convergence measure: the
+ * largest relative L2 change between input and output of the density, the
+ * three momentum components and the total energy density over the fluid
+ * cells, as kgs_iterate reports it.
+ *
+ * The call copies small tables from host memory, launches the iteration and
+ * reads the residual back, then blocks the host until the iteration has
+ * finished on the GPU.  Those copies and that wait cannot be recorded in a
+ * CUDA graph: the call must never be made while `stream` (or the device) is
+ * being captured.
  *
  * No cudaMalloc, cudaFree or other allocating routine is called: every
  * intermediate buffer lives in one file-scope device array of
@@ -377,10 +442,9 @@ int kgs_surrogate_apply(long long ncell, const double *up, const float *y, doubl
  * with KGS_EINVAL (roughly: face planes (nx ny + ny nz + nz nx) * nvel and
  * moment partials 8 * 16 * ncell * ceil(nvel_octant / 128) words must fit).
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  All calls share
- * the array and each call overwrites it: calls that overlap on the GPU
- * (concurrent streams or host threads) race and must be serialised by the
- * caller.
+ * device).  All calls share the array and each call overwrites it: calls
+ * that overlap on the GPU (concurrent streams or host threads) race and must
+ * be serialised by the caller.
  * Returns KGS_OK, KGS_EDIVERGED (outputs hold the offending iterate),
  * KGS_EINVAL, KGS_ECUDA. */
 #define KGS_NOALLOC_SCRATCH_BYTES (64u << 20)

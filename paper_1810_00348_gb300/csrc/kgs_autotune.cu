@@ -84,7 +84,9 @@ int time_shape(const kgs_problem *p, int precision, int vpc, int bz, double *ms)
     const int timed = 2;
     auto one = [&]() -> int {
         int r;
-        if ((r = ctx_launch_coef(c)) || (r = ctx_launch_stages(c)) || (r = ctx_launch_closure(c, c->resid))) return r;
+        if ((r = ctx_launch_coef(c)) || (r = ctx_launch_stages(c)) || (r = ctx_launch_sums(c)) ||
+            (r = ctx_launch_closure(c, c->resid, nullptr)))
+            return r;
         std::swap(c->mac, c->mac_new);
         std::swap(c->rho_w, c->rho_w_new);
         return KGS_OK;

@@ -38,6 +38,13 @@ struct kgs_batch {
     int n_items = 0;
     int *d_counter = nullptr, *d_flags = nullptr, *d_flag_off = nullptr, *d_error = nullptr;
     size_t n_flags = 0;
+    int *d_pos = nullptr;               // place of each item in its accumulator chain
+    size_t pos_cap = 0;
+    int *d_tok = nullptr;               // chain tokens of all instances
+    size_t n_tok = 0;
+    std::vector<size_t> tok_off;        // first token of each instance
+    void *d_scratch = nullptr;          // per-CTA moment partials
+    size_t scratch_stride = 0;
     double *d_resid = nullptr;  // [2 n] + error word
     double *h_resid = nullptr;  // pinned copy
     int grid = 0;
@@ -92,15 +99,30 @@ int build_items(kgs_batch *b)
         KGS_CHECK(cudaMalloc(&b->d_items, items.size() * sizeof(int4)));
         b->items_cap = items.size();
     }
-    if (!items.empty())
+    std::vector<const HostTables *> tabs(b->n);
+    for (int i = 0; i < b->n; i++) tabs[i] = &b->ctx[i]->t;
+    std::vector<int> pos;
+    chain_positions(items, tabs, pos);
+    if (pos.size() > b->pos_cap) {
+        if (b->d_pos) cudaFree(b->d_pos);
+        b->d_pos = nullptr;
+        KGS_CHECK(cudaMalloc(&b->d_pos, pos.size() * sizeof(int)));
+        b->pos_cap = pos.size();
+    }
+    if (!items.empty()) {
         KGS_CHECK(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        KGS_CHECK(cudaMemcpy(b->d_pos, pos.data(), pos.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     return KGS_OK;
 }
 
 int upload_args(kgs_batch *b, int which)
 {
     std::vector<SweepArgs> args(b->n);
-    for (int i = 0; i < b->n; i++) args[i] = ctx_sweep_args(b->ctx[i]);
+    for (int i = 0; i < b->n; i++) {
+        args[i] = ctx_sweep_args(b->ctx[i]);
+        args[i].tok = b->d_tok + b->tok_off[i];
+    }
     KGS_CHECK(cudaMemcpy(b->d_args[which], args.data(), args.size() * sizeof(SweepArgs), cudaMemcpyHostToDevice));
     return KGS_OK;
 }
@@ -115,6 +137,7 @@ int enqueue_iteration(kgs_batch *b, int which)
     KGS_CHECK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
     KGS_CHECK(cudaMemsetAsync(b->d_flags, 0, b->n_flags * sizeof(int), st));
     KGS_CHECK(cudaMemsetAsync(b->d_error, 0, sizeof(int), st));
+    KGS_CHECK(cudaMemsetAsync(b->d_tok, 0, b->n_tok * sizeof(int), st));
     BatchSweepArgs ba;
     ba.inst = b->d_args[which];
     ba.items = b->d_items;
@@ -122,6 +145,9 @@ int enqueue_iteration(kgs_batch *b, int which)
     ba.counter = b->d_counter;
     ba.flags = b->d_flags;
     ba.flag_off = b->d_flag_off;
+    ba.pos = b->d_pos;
+    ba.scratch = b->d_scratch;
+    ba.scratch_stride = b->scratch_stride;
     ba.error = b->d_error;
     ba.spin_limit = b->spin_limit;
     ba.skip_publish = b->skip_publish;
@@ -130,7 +156,9 @@ int enqueue_iteration(kgs_batch *b, int which)
     KGS_CHECK(launch_sweep_persistent(b->precision, b->tv, b->line16, b->uniform, ba, b->nxo_max, b->grid, st));
     KGS_CHECK(cudaEventRecordWithFlags(b->ev[1], st, cudaEventRecordExternal));
     for (int i = 0; i < b->n; i++)
-        if (b->active[i] && (rc = ctx_launch_closure(b->ctx[i], b->d_resid + 2 * i))) return rc;
+        if (b->active[i] &&
+            ((rc = ctx_launch_sums(b->ctx[i])) || (rc = ctx_launch_closure(b->ctx[i], b->d_resid + 2 * i, nullptr))))
+            return rc;
     KGS_CHECK(cudaMemcpyAsync(b->h_resid, b->d_resid, (2 * b->n + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
     return KGS_OK;
 }
@@ -173,13 +201,69 @@ void free_batch(kgs_batch *b)
         }
     b->ctx.clear();
     // d_error lives inside d_resid
-    void *bufs[] = {b->d_args[0], b->d_args[1], b->d_items, b->d_counter, b->d_flags, b->d_flag_off, b->d_resid};
+    void *bufs[] = {b->d_args[0], b->d_args[1], b->d_items, b->d_counter, b->d_flags, b->d_flag_off, b->d_resid,
+                    b->d_pos, b->d_tok, b->d_scratch};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (b->h_resid) cudaFreeHost(b->h_resid);
     for (auto &e : b->ev)
         if (e) cudaEventDestroy(e);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+// One outer iteration of the active instances (graph replay).  count and
+// last receive, per instance, the iterations run and the last residual;
+// retire: instances below the tolerance leave the work list.  Returns false
+// when nothing is active or an error (rc) stops the run.
+bool batch_step(kgs_batch *b, bool retire, std::vector<int> &count, std::vector<double> &last, int &rc)
+{
+    bool any = false;
+    for (int i = 0; i < b->n; i++) any |= b->active[i] != 0;
+    if (!any) return false;
+    if (b->dirty && (rc = rebuild(b))) return false;
+    const int which = b->next;
+    cudaError_t e = cudaGraphLaunch(b->exec[which], b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        rc = cuda_err(e);
+        return false;
+    }
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+    if (e != cudaSuccess) {
+        rc = cuda_err(e);
+        return false;
+    }
+    b->sweep_ms += ms;
+    b->sweeps++;
+    const int *err = reinterpret_cast<const int *>(b->h_resid + 2 * b->n);
+    if (*err) {
+        rc = KGS_ETIMEOUT;
+        return false;
+    }
+    bool bad = false, retired = false;
+    for (int i = 0; i < b->n; i++) {
+        if (!b->active[i]) continue;
+        const double r = b->h_resid[2 * i];
+        bad |= b->h_resid[2 * i + 1] != 0.0;
+        ctx_finish(b->ctx[i], r);
+        b->kernel_launches += 6;  // coefficients, sums, four closure kernels
+        count[i]++;
+        b->done[i]++;
+        last[i] = r;
+        if (retire && r < b->tol) {
+            b->active[i] = 0;
+            retired = true;
+        }
+    }
+    b->kernel_launches += 1;
+    b->next = 1 - which;
+    if (retired) b->dirty = true;
+    if (bad) {
+        rc = KGS_EDIVERGED;
+        return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -238,11 +322,14 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
         o.stream = b->stream;
         o.wall_norm = p.wall_norm;
         o.mass_rescale = p.mass_rescale;
+        o.q_lagged = p.q_lagged;
         o.v_per_cta = vpc;
         o.block_z = bz;
         int rc = ctx_create(&b->ctx[i], &p.grid, p.solid, &p.vgrid, &p.gas, &p.bc, &o);
-        if (rc) return fail(rc);
+        if (rc || (rc = ctx_alloc_acc(b->ctx[i]))) return fail(rc);
         const HostTables &t = b->ctx[i]->t;
+        b->tok_off.push_back(b->n_tok);
+        b->n_tok += ctx_n_tokens(t);
         b->tv = t.tv;
         b->bz = t.bz;
         b->nxo_max = std::max(b->nxo_max, t.nxo_max);
@@ -260,6 +347,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
         cudaMalloc(&b->d_flags, std::max<size_t>(b->n_flags, 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&b->d_flag_off, n * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&b->d_resid, (2 * n + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->d_tok, b->n_tok * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&b->h_resid, (2 * n + 1) * sizeof(double)) != cudaSuccess)
         return fail(KGS_ENOMEM);
     // the error word shares the residual buffer so one copy brings both back
@@ -275,6 +363,8 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     per_sm = sweep_persistent_occupancy(b->precision, b->tv, b->line16, b->uniform, smem);
     if (per_sm < 1) return fail(KGS_ECUDA);
     b->grid = sms * per_sm;
+    b->scratch_stride = sweep_scratch_bytes(b->bz);
+    if (cudaMalloc(&b->d_scratch, (size_t)b->grid * b->scratch_stride) != cudaSuccess) return fail(KGS_ENOMEM);
     *out = b;
     return KGS_OK;
 }
@@ -298,54 +388,8 @@ int kgs_batch_iterate(kgs_batch *b, int n_iters, int *iters_done, double *residu
             }
     }
     int rc = KGS_OK;
-    for (int k = 0; k < limit; k++) {
-        bool any = false;
-        for (int i = 0; i < b->n; i++) any |= b->active[i] != 0;
-        if (!any) break;
-        if (b->dirty && (rc = rebuild(b))) break;
-        const int which = b->next;
-        cudaError_t e = cudaGraphLaunch(b->exec[which], b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) {
-            rc = cuda_err(e);
-            break;
-        }
-        float ms = 0.f;
-        e = cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
-        if (e != cudaSuccess) {
-            rc = cuda_err(e);
-            break;
-        }
-        b->sweep_ms += ms;
-        b->sweeps++;
-        const int *err = reinterpret_cast<const int *>(b->h_resid + 2 * b->n);
-        if (*err) {
-            rc = KGS_ETIMEOUT;
-            break;
-        }
-        bool bad = false, retire = false;
-        for (int i = 0; i < b->n; i++) {
-            if (!b->active[i]) continue;
-            const double r = b->h_resid[2 * i];
-            bad |= b->h_resid[2 * i + 1] != 0.0;
-            ctx_finish(b->ctx[i], r);
-            b->kernel_launches += 5;
-            count[i]++;
-            b->done[i]++;
-            last[i] = r;
-            if (until && r < b->tol) {
-                b->active[i] = 0;
-                retire = true;
-            }
-        }
-        b->kernel_launches += 1;
-        b->next = 1 - which;
-        if (retire) b->dirty = true;
-        if (bad) {
-            rc = KGS_EDIVERGED;
-            break;
-        }
-    }
+    for (int k = 0; k < limit; k++)
+        if (!batch_step(b, until, count, last, rc)) break;
     if (rc == KGS_OK && until)
         for (int i = 0; i < b->n; i++)
             if (!(last[i] >= 0.0 && last[i] < b->tol)) rc = KGS_NOTCONVERGED;
@@ -354,6 +398,96 @@ int kgs_batch_iterate(kgs_batch *b, int n_iters, int *iters_done, double *residu
     if (residuals)
         for (int i = 0; i < b->n; i++) residuals[i] = last[i];
     return rc;
+}
+
+int kgs_batch_solve(kgs_batch **out, int n, const kgs_problem *probs, const kgs_opts *opts, int *iters_mixed,
+                    int *iters_fp64, double *residuals)
+{
+    if (!out || n < 1 || !probs || !opts || !(opts->tol > 0.0)) return KGS_EINVAL;
+    *out = nullptr;
+    const int budget = opts->max_iters > 0 ? opts->max_iters : 1000;
+    kgs_batch *m = nullptr, *d = nullptr;
+    auto finish = [&](int code) {
+        if (m) kgs_batch_destroy(m);
+        if (code != KGS_OK && code != KGS_NOTCONVERGED && d) {
+            kgs_batch_destroy(d);
+            d = nullptr;
+        }
+        *out = d;
+        return code;
+    };
+    // mixed phase: every instance runs until it reaches tol or stops making
+    // progress (the rule of kgs_solve, per instance), then retires
+    kgs_opts om = *opts;
+    om.precision = KGS_MIXED;
+    int rc = kgs_batch_setup(&m, n, probs, &om);
+    if (rc) return finish(rc);
+    if (cudaSetDevice(m->dev) != cudaSuccess) return finish(KGS_ECUDA);
+    std::vector<int> nm(n, 0), stalled(n, 0), nd(n, 0);
+    std::vector<double> best(n, 1e300), last(n, -1.0);
+    for (;;) {
+        bool any = false;
+        for (int i = 0; i < n; i++) any |= m->active[i] != 0;
+        if (!any) break;
+        std::vector<int> count(n, 0);
+        for (int k = 0; k < SOLVE_CHUNK; k++)
+            if (!batch_step(m, false, count, last, rc)) break;
+        if (rc) return finish(rc);
+        for (int i = 0; i < n; i++) {
+            if (!m->active[i]) continue;
+            nm[i] += count[i];
+            const double r = last[i];
+            bool retire = r < opts->tol || nm[i] >= budget;
+            if (!retire) {
+                if (r < SOLVE_PROGRESS * best[i])
+                    stalled[i] = 0;
+                else if (++stalled[i] >= (r < SOLVE_NEAR_FLOOR ? SOLVE_PATIENCE : SOLVE_PATIENCE_FAR))
+                    retire = true;
+                best[i] = std::min(best[i], r);
+            }
+            if (retire) {
+                m->active[i] = 0;
+                m->dirty = true;
+            }
+        }
+    }
+    // FP64 phase from each mixed state (macros, wall densities, mass target)
+    kgs_opts od = *opts;
+    od.precision = KGS_FP64;
+    od.v_per_cta = 128;
+    od.block_z = opts->block_z > 0 ? opts->block_z : 32;
+    if ((rc = kgs_batch_setup(&d, n, probs, &od))) return finish(rc);
+    std::vector<unsigned char> state;
+    for (int i = 0; i < n; i++) {
+        size_t len = 0;
+        if ((rc = kgs_save(m->ctx[i], nullptr, &len))) return finish(rc);
+        state.resize(len);
+        if ((rc = kgs_save(m->ctx[i], state.data(), &len)) || (rc = kgs_load(d->ctx[i], state.data(), len)))
+            return finish(rc);
+        // every instance with budget left runs at least one FP64 iteration
+        // (it confirms the tolerance), at most max(1, budget - mixed iterations)
+        d->active[i] = nm[i] < budget;
+    }
+    d->dirty = true;
+    std::vector<int> count(n, 0);
+    std::vector<double> dl(last);
+    for (;;) {
+        if (!batch_step(d, true, count, dl, rc)) break;
+        for (int i = 0; i < n; i++)
+            if (d->active[i] && count[i] >= std::max(1, budget - nm[i])) {
+                d->active[i] = 0;
+                d->dirty = true;
+            }
+    }
+    if (rc) return finish(rc);
+    int status = KGS_OK;
+    for (int i = 0; i < n; i++) {
+        if (iters_mixed) iters_mixed[i] = nm[i];
+        if (iters_fp64) iters_fp64[i] = count[i];
+        if (residuals) residuals[i] = dl[i];
+        if (!(dl[i] >= 0.0 && dl[i] < opts->tol)) status = KGS_NOTCONVERGED;
+    }
+    return finish(status);
 }
 
 int kgs_batch_moments(kgs_batch *b, int i, double *out)

@@ -1,7 +1,9 @@
 // kgs_closure.cu -- per-iteration kernels around the sweep (arXiv 1810.00348):
 //   coef_kernel      lagged cell coefficients of Eq. (2) and tau = mu/p (Eq. (10))
-//   close_kernel     fixed-order sum of the per-group partials, the macroscopic
-//                    update of Eq. (5) and the wall densities of Eq. (9)
+//   part_sums        fixed-order sum of the staged sweep's per-group partials
+//   acc_sums         fixed-order sum of the persistent sweep's accumulators
+//   closure          the macroscopic update of Eq. (5) and the wall densities
+//                    of Eq. (9) from the per-cell sums
 //   finalize_mass    global mass and the Section 3.4 rescale factor
 //   scale_residual   rescale, divergence check and the Section 4.1 residual
 //   finalize_residual
@@ -104,33 +106,76 @@ struct FFSum {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// Closure of one outer iteration for CLOSE_CELLS cells per block.  The sums
-// come first: the first 13 warps hold (cell, moment slot) pairs, each thread
-// summing one slot of one cell over all velocity groups in group order (a
-// cell's slots are contiguous, so a warp's loads cover a few 128-byte rows);
-// the last 3 warps hold (cell, axis) pairs for the incoming wall fluxes,
-// which split by the side of the group's octant.  The two kinds never share
-// a warp, so neither takes the other's branch.  Then one thread per cell
-// turns the sums into the macroscopic fields and wall densities.
+// Sum w M_ref (xi_x - Ux)^a (xi_y - Uy)^b (xi_z - Uz)^c of the reference
+// Maxwellian over the swept velocities: the binomial expansion of its raw
+// moments about the cell's lagged velocity U.
+__device__ double ref_central(const RefMoments &r, int a, int b, int c, const double U[3])
+{
+    const double binom[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
+    double s = 0.0;
+    for (int i = 0; i <= a; i++)
+        for (int j = 0; j <= b; j++)
+            for (int k = 0; k <= c; k++) {
+                double f = binom[a][i] * binom[b][j] * binom[c][k];
+                for (int e = i; e < a; e++) f *= -U[0];
+                for (int e = j; e < b; e++) f *= -U[1];
+                for (int e = k; e < c; e++) f *= -U[2];
+                s += f * r.raw[ref_index(i, j, k)];
+            }
+    return s;
+}
+
+// The reference Maxwellian's part of sum slot q (< SUM_F0) about U.
+__device__ double ref_slot(const RefMoments &r, int q, const double U[3])
+{
+    switch (q) {
+    case P_S0: return ref_central(r, 0, 0, 0, U);
+    case P_S1X: return ref_central(r, 1, 0, 0, U);
+    case P_S1Y: return ref_central(r, 0, 1, 0, U);
+    case P_S1Z: return ref_central(r, 0, 0, 1, U);
+    case P_S2XX: return ref_central(r, 2, 0, 0, U);
+    case P_S2YY: return ref_central(r, 0, 2, 0, U);
+    case P_S2ZZ: return ref_central(r, 0, 0, 2, U);
+    case P_S2XY: return ref_central(r, 1, 1, 0, U);
+    case P_S2XZ: return ref_central(r, 1, 0, 1, U);
+    case P_S2YZ: return ref_central(r, 0, 1, 1, U);
+    case P_S3X: return ref_central(r, 3, 0, 0, U) + ref_central(r, 1, 2, 0, U) + ref_central(r, 1, 0, 2, U);
+    case P_S3Y: return ref_central(r, 2, 1, 0, U) + ref_central(r, 0, 3, 0, U) + ref_central(r, 0, 1, 2, U);
+    default: return ref_central(r, 2, 0, 1, U) + ref_central(r, 0, 2, 1, U) + ref_central(r, 0, 0, 3, U);
+    }
+}
+
+// Lagged velocity centre of cell c as the FP32 sweep used it.
+__device__ __forceinline__ void centre32(const void *coef, size_t c, double U[3])
+{
+    const float *cf = static_cast<const float *>(coef) + c * NCOEF;
+    U[0] = -0.5 * (double)cf[C_M2UX];
+    U[1] = -0.5 * (double)cf[C_M2UY];
+    U[2] = -0.5 * (double)cf[C_M2UZ];
+}
+
+// Per-cell sums of the staged sweep's partials for CLOSE_CELLS cells per block:
+// the first 13 warps hold (cell, moment slot) pairs, each thread summing one
+// slot of one cell over all velocity groups in group order (a cell's slots
+// are contiguous, so a warp's loads cover a few 128-byte rows); the last 3
+// warps hold (cell, axis) pairs for the incoming wall fluxes, which split by
+// the side of the group's octant.  The two kinds never share a warp, so
+// neither takes the other's branch.
 static_assert(CLOSE_CELLS * 13 % 32 == 0 && CLOSE_CELLS * 3 % 32 == 0, "slot warps must not mix");
 template <typename Real>
-__global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseArgs a)
+__global__ void __launch_bounds__(CLOSE_CELLS * NPART) part_sums_kernel(const PartSumArgs a)
 {
-    constexpr int NS = 13 + 6;  // 13 sums about U^n, incoming flux per side
-    __shared__ double sS[CLOSE_CELLS][NS];
     const size_t ncell = a.ncell;
-    {
     const int t = threadIdx.x;
     const bool flux = t >= CLOSE_CELLS * P_FX;  // uniform per warp
     const int cl = flux ? (t - CLOSE_CELLS * P_FX) / 3 : t / P_FX;
     const int axis = flux ? (t - CLOSE_CELLS * P_FX) % 3 : 0;  // flux slots: incoming flux along x, y, z
     const int q = flux ? P_FX + axis : t % P_FX;
     const size_t c = (size_t)blockIdx.x * CLOSE_CELLS + cl;
-    const bool live = c < ncell && !(a.solid && a.solid[c]);
-    if (live) {
-        double sum, f_minus, f_plus;
+    if (c >= ncell) return;
+    double sum = 0.0, f_minus = 0.0, f_plus = 0.0;
+    if (!(a.solid && a.solid[c])) {
         if (sizeof(Real) == 8) {
-            sum = f_minus = f_plus = 0.0;
             const double *pp = static_cast<const double *>(a.part) + c * NPART + q;
             if (!flux) {
 #pragma unroll 4
@@ -186,29 +231,88 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
             }
             sum = f_minus = acc0.value();
             f_plus = acc1.value();
+            // the FP32 sweep summed g = f - M_ref: add the reference's part
+            if (!flux) {
+                double U[3];
+                centre32(a.coef, c, U);
+                sum += ref_slot(a.ref, q, U);
+            } else {
+                if (a.wall_kind[(size_t)(2 * axis) * ncell + c] >= 0) f_minus += a.ref.flux[2 * axis];
+                if (a.wall_kind[(size_t)(2 * axis + 1) * ncell + c] >= 0) f_plus += a.ref.flux[2 * axis + 1];
+            }
         }
-        if (!flux) {
-            sS[cl][q] = sum;
+    }
+    if (!flux) {
+        a.sums[(size_t)q * ncell + c] = sum;
+    } else {
+        a.sums[(size_t)(SUM_F0 + 2 * axis) * ncell + c] = f_minus;
+        a.sums[(size_t)(SUM_F0 + 2 * axis + 1) * ncell + c] = f_plus;
+    }
+}
+
+// Per-cell sums of the persistent sweep's ordered accumulators: thread
+// (cell, slot) adds the nacc accumulators of its slot in accumulator order
+// (float-float for the FP32 path) and writes the FP64 sum.
+template <typename Real>
+__global__ void __launch_bounds__(256) acc_sums_kernel(const AccSumArgs a)
+{
+    const size_t ncell = a.ncell;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncell * NACC) return;
+    const size_t c = i / NACC;
+    const int q = (int)(i % NACC);
+    if (q >= NSUM) return;
+    double v = 0.0;
+    if (!(a.solid && a.solid[c])) {
+        if (sizeof(Real) == 8) {
+            const double *p = static_cast<const double *>(a.acc) + i;
+            for (int k = 0; k < a.nacc; k++) v += p[(size_t)k * ncell * NACC];
         } else {
-            sS[cl][13 + 2 * axis] = f_minus;
-            sS[cl][13 + 2 * axis + 1] = f_plus;
+            const float2 *p = static_cast<const float2 *>(a.acc) + i;
+            FFSum t;
+            for (int k = 0; k < a.nacc; k++) {
+                const float2 e = p[(size_t)k * ncell * NACC];
+                t.add(e.x, 0.f);
+                t.add(e.y, 0.f);
+            }
+            v = t.value();
+            // the FP32 sweep summed g = f - M_ref: add the reference's part
+            if (q < SUM_F0) {
+                double U[3];
+                centre32(a.coef, c, U);
+                v += ref_slot(a.ref, q, U);
+            } else if (a.wall_kind[(size_t)(q - SUM_F0) * ncell + c] >= 0) {
+                v += a.ref.flux[q - SUM_F0];
+            }
         }
     }
-    }
-    __syncthreads();
-    // one thread per cell from here on
-    if (threadIdx.x >= CLOSE_CELLS) return;
-    const int cl = threadIdx.x;
-    const size_t c = (size_t)blockIdx.x * CLOSE_CELLS + cl;
+    a.sums[(size_t)q * ncell + c] = v;
+}
+
+// Closure of one outer iteration, one thread per cell (CLOSE_CELLS cells per
+// block): the sums about U^n become the macroscopic fields of step n+1 and
+// the wall densities (Eq. (5), Eq. (9)); the block's cell masses are summed
+// in a fixed order for the Section 3.4 rescale.
+__global__ void __launch_bounds__(CLOSE_CELLS) closure_kernel(const ClosureArgs a)
+{
+    const size_t ncell = a.ncell;
+    const size_t c = (size_t)blockIdx.x * CLOSE_CELLS + threadIdx.x;
     const bool live = c < ncell && !(a.solid && a.solid[c]);
     double mass = 0.0;
     if (live) {
-        const double *S = sS[cl];
-        const double *F = sS[cl] + 13;
-        const Real *cf = static_cast<const Real *>(a.coef) + c * NCOEF;
+        double S[NSUM];
+        for (int q = 0; q < NSUM; q++) S[q] = a.sums[(size_t)q * ncell + c];
         // The sums were taken about the lagged velocity U^n as stored in the
         // sweep precision; shift exactly to U^{n+1} = U^n + delta.
-        const double Uc[3] = {-0.5 * (double)cf[C_M2UX], -0.5 * (double)cf[C_M2UY], -0.5 * (double)cf[C_M2UZ]};
+        double m2u[3];
+        if (a.precision == 0) {
+            const double *cf = static_cast<const double *>(a.coef) + c * NCOEF;
+            m2u[0] = cf[C_M2UX], m2u[1] = cf[C_M2UY], m2u[2] = cf[C_M2UZ];
+        } else {
+            const float *cf = static_cast<const float *>(a.coef) + c * NCOEF;
+            m2u[0] = cf[C_M2UX], m2u[1] = cf[C_M2UY], m2u[2] = cf[C_M2UZ];
+        }
+        const double Uc[3] = {-0.5 * m2u[0], -0.5 * m2u[1], -0.5 * m2u[2]};
         const double rho = S[P_S0];
         const double d[3] = {S[P_S1X] / rho, S[P_S1Y] / rho, S[P_S1Z] / rho};
         const double S2[3][3] = {{S[P_S2XX], S[P_S2XY], S[P_S2XZ]},
@@ -225,9 +329,15 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
         const double T = trP / (3.0 * rho * R_GAS);
         double qf[3];
         for (int i = 0; i < 3; i++) {
-            // q_i = 1/2 sum w f (c'-delta)_i |c'-delta|^2 expanded in the sums about U^n
-            const double S2d = S2[i][0] * d[0] + S2[i][1] * d[1] + S2[i][2] * d[2];
-            qf[i] = 0.5 * (S3[i] - 2.0 * S2d - d[i] * trS2 + 2.0 * d[i] * dS1 + d2 * S1[i] - rho * d2 * d[i]);
+            if (a.q_lagged) {
+                // the heat flux about the lagged velocity U^n (Algorithm 3's
+                // eight moments, exact only at the fixed point)
+                qf[i] = 0.5 * S3[i];
+            } else {
+                // q_i = 1/2 sum w f (c'-delta)_i |c'-delta|^2 expanded in the sums about U^n
+                const double S2d = S2[i][0] * d[0] + S2[i][1] * d[1] + S2[i][2] * d[2];
+                qf[i] = 0.5 * (S3[i] - 2.0 * S2d - d[i] * trS2 + 2.0 * d[i] * dS1 + d2 * S1[i] - rho * d2 * d[i]);
+            }
         }
         double *mn = a.mac_new;
         mn[c] = rho;
@@ -240,7 +350,7 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
         mn[7 * ncell + c] = qf[2];
         for (int s = 0; s < 6; s++) {
             const int kind = a.wall_kind[s * ncell + c];
-            a.rho_w_new[s * ncell + c] = kind >= 0 ? F[s] * a.wall_norm[kind * 6 + s] : 0.0;
+            a.rho_w_new[s * ncell + c] = kind >= 0 ? S[SUM_F0 + s] * a.wall_norm[kind * 6 + s] : 0.0;
         }
         const int i = (int)(c % a.nx), j = (int)((c / a.nx) % a.ny), k = (int)(c / ((size_t)a.nx * a.ny));
         mass = rho * a.dx[i] * a.dy[j] * a.dz[k];
@@ -249,9 +359,8 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) close_kernel(const CloseA
         for (int s = 0; s < 6; s++) a.rho_w_new[s * ncell + c] = 0.0;
     }
     // fixed-order sum of the block's cell masses (lanes 0 .. CLOSE_CELLS-1)
-    static_assert(CLOSE_CELLS <= 32, "one warp per block's cells");
-    constexpr unsigned mask = CLOSE_CELLS == 32 ? 0xffffffffu : (1u << CLOSE_CELLS) - 1u;
-    for (int off = CLOSE_CELLS / 2; off > 0; off >>= 1) mass += __shfl_down_sync(mask, mass, off, CLOSE_CELLS);
+    static_assert(CLOSE_CELLS == 32, "one warp per block's cells");
+    for (int off = 16; off > 0; off >>= 1) mass += __shfl_down_sync(0xffffffffu, mass, off);
     if (threadIdx.x == 0) a.blk_mass[blockIdx.x] = mass;
 }
 
@@ -446,13 +555,29 @@ cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_close(const CloseArgs &a, cudaStream_t s)
+cudaError_t launch_part_sums(const PartSumArgs &a, cudaStream_t s)
 {
     const unsigned nb = (unsigned)close_blocks(a.ncell);
     if (a.precision == 0)
-        close_kernel<double><<<nb, CLOSE_CELLS * NPART, 0, s>>>(a);
+        part_sums_kernel<double><<<nb, CLOSE_CELLS * NPART, 0, s>>>(a);
     else
-        close_kernel<float><<<nb, CLOSE_CELLS * NPART, 0, s>>>(a);
+        part_sums_kernel<float><<<nb, CLOSE_CELLS * NPART, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acc_sums(const AccSumArgs &a, cudaStream_t s)
+{
+    const unsigned nb = nblk((size_t)a.ncell * NACC, 256);
+    if (a.precision == 0)
+        acc_sums_kernel<double><<<nb, 256, 0, s>>>(a);
+    else
+        acc_sums_kernel<float><<<nb, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_closure(const ClosureArgs &a, cudaStream_t s)
+{
+    closure_kernel<<<(unsigned)close_blocks(a.ncell), CLOSE_CELLS, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@ struct kgs_ctx {
     cudaStream_t stream = nullptr;
     kgs::HostTables t;
     int mass_rescale = 0;
+    int q_lagged = 0;       // heat flux about the lagged velocity (closure option)
     int max_iters = 1000;
     double tol = 1e-8;
     double M0 = 0.0;
@@ -24,7 +25,10 @@ struct kgs_ctx {
     double *mac = nullptr, *mac_new = nullptr, *rho_w = nullptr, *rho_w_new = nullptr;
     void *coef = nullptr, *vel = nullptr, *velm = nullptr, *mtab = nullptr, *FX = nullptr, *FY = nullptr,
          *FZ = nullptr;
-    void *part = nullptr;
+    void *part = nullptr;   // staged sweep only: per-(group, cell) partials
+    void *acc = nullptr;    // persistent sweep: ordered accumulators [nacc][ncell][NACC]
+    int use_acc = 0;        // the sweep runs persistent and adds into acc
+    double *sums = nullptr; // [NSUM][ncell] per-cell sums of the iteration (FP64)
     double *vel64 = nullptr, *axis64 = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;
     double *ddx = nullptr, *ddy = nullptr, *ddz = nullptr;
     uint8_t *solid = nullptr, *side_flags = nullptr;
@@ -43,6 +47,10 @@ struct kgs_ctx {
     int4 *p_items = nullptr;
     int *p_counter = nullptr, *p_flags = nullptr, *p_flag_off = nullptr;
     size_t p_n_flags = 0;
+    int *p_pos = nullptr;             // place of each item in its accumulator chain
+    int *p_tok = nullptr;             // chain tokens [nacc][nbz][nby][nbx]
+    void *p_scratch = nullptr;        // per-CTA moment partials
+    size_t scratch_stride = 0;
     kgs::SweepArgs *p_args = nullptr, *h_args = nullptr;  // device copy, pinned host staging
     long long spin_limit = 20000000;  // polls of ~100 ns before a wait gives up
     size_t device_bytes = 0;
@@ -57,6 +65,17 @@ struct kgs_ctx {
 
 namespace kgs {
 
+// Switch rule of the mixed-then-FP64 solves: mixed iterations run in chunks;
+// an instance leaves the mixed phase once its residual has not fallen below
+// SOLVE_PROGRESS x its best value for SOLVE_PATIENCE chunks while below
+// SOLVE_NEAR_FLOOR (SOLVE_PATIENCE_FAR chunks above it, where small-Kn solves
+// can first rise for a while).
+constexpr int SOLVE_CHUNK = 5;
+constexpr int SOLVE_PATIENCE = 2;
+constexpr double SOLVE_NEAR_FLOOR = 1e-3;
+constexpr int SOLVE_PATIENCE_FAR = 20;
+constexpr double SOLVE_PROGRESS = 0.9;
+
 int cuda_err(cudaError_t e);
 
 // Build a context on the current device and `stream` (validated inputs).
@@ -68,14 +87,26 @@ SweepArgs ctx_sweep_args(const kgs_ctx *c);
 // order the persistent sweep claims them: (inst, octant << 24 | group,
 // reflected block coordinates packed 10 bits each, global group index).
 void ctx_stage_items(const HostTables &t, int inst, int stage, std::vector<int4> &out);
-// Set up the persistent sweep of a standalone context (items, flags, grid).
+// Set up the persistent sweep of a standalone context (items, flags, chain
+// tokens, scratch, grid), or the staged sweep's partials if the persistent
+// kernel cannot be resident.
 int ctx_persist_init(kgs_ctx *c);
+// Ordered accumulators of a context whose sweep runs persistent.
+int ctx_alloc_acc(kgs_ctx *c);
+// Chain tokens per (accumulator, block) of one instance.
+inline size_t ctx_n_tokens(const HostTables &t) { return (size_t)t.nacc * t.nbx * t.nby * t.nbz; }
+// Place of every item of a stage-ordered work list in its accumulator chain
+// (items of one (instance, accumulator, block), in list order).
+void chain_positions(const std::vector<int4> &items, const std::vector<const HostTables *> &tabs,
+                     std::vector<int> &pos);
 // Phases of one outer iteration (asynchronous on the context's stream).
 int ctx_launch_coef(kgs_ctx *c);
 int ctx_launch_stages(kgs_ctx *c);
-// Closure into the new buffers; the residual and divergence flag go to
-// resid_dev[0..1] (device).
-int ctx_launch_closure(kgs_ctx *c, double *resid_dev);
+// Per-cell sums of the swept velocities into c->sums.
+int ctx_launch_sums(kgs_ctx *c);
+// Closure from the per-cell sums (sums = NULL: c->sums) into the new buffers;
+// the residual and divergence flag go to resid_dev[0..1] (device).
+int ctx_launch_closure(kgs_ctx *c, double *resid_dev, const double *sums);
 // After the iteration's work has completed: swap the state buffers.
 void ctx_finish(kgs_ctx *c, double residual);
 

@@ -49,6 +49,32 @@ enum {
     P_S3X, P_S3Y, P_S3Z, P_FX, P_FY, P_FZ
 };
 
+// Per-cell sums of one outer iteration as the closure reads them ([NSUM][ncell],
+// FP64): the 13 sums about U^n in the P_* order, then the incoming flux onto
+// the wall on each domain side s (-x, +x, -y, +y, -z, +z) at slot SUM_F0 + s.
+constexpr int SUM_F0 = 13;
+constexpr int NSUM = 19;
+// Ordered accumulators of the persistent sweep: [nacc][ncell][NACC] (FP64, or
+// float-float pairs (hi, lo) for the FP32 path); slots as the sums above.
+constexpr int NACC = 20;
+constexpr int NACC_MAX = 8;  // accumulators per instance, at most
+
+// Reference Maxwellian of the FP32 sweep, which carries g = f - M_ref rather
+// than f: the moments of the FP32 table values of M_ref over the swept
+// velocities, raw[a][b][c] = sum w M_ref xi_x^a xi_y^b xi_z^c (a + b + c <= 3,
+// index ref_index), and their incoming flux onto each domain side.  All zero
+// for the FP64 path, which carries f itself.
+constexpr int NREF = 20;
+__host__ __device__ constexpr int ref_index(int a, int b, int c)
+{
+    // a + b + c = n occupies [n (n+1) (n+2) / 6, ...), ordered by (b + c, c)
+    return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + (b + c) * (b + c + 1) / 2 + c;
+}
+struct RefMoments {
+    double raw[NREF];
+    double flux[6];
+};
+
 // Wall-Maxwellian table rows: 0..5 domain side, 6 solid surface, 7 free stream.
 constexpr int MT_SOLID = 6;
 constexpr int MT_INFLOW = 7;
@@ -64,8 +90,9 @@ struct SweepArgs {
     int Nv;                       // all velocities
     int vg_size;                  // velocities per CTA
     const void *vel;              // Real[Nv][4]: xi_x, xi_y, xi_z, w (octant-sorted)
-    const void *velm;             // Real[Nv][8]: w_x, w_y w_z, and the low parts of xi_x, xi_y,
-                                  // xi_z (xi = hi + lo with hi = the value in vel), 3 unused
+    const void *velm;             // Real[Nv][8]: w_x, w_y w_z, the low parts of xi_x, xi_y, xi_z
+                                  // (xi = hi + lo with hi = the value in vel), M_ref (FP32
+                                  // path; 0 for FP64), 2 unused
     int oct_nx[8];                // x nodes in each octant (length of its velocity x-lines)
     int nxo_max;                  // max over octants of oct_nx
     int any_solid;                // the problem has solid cells
@@ -74,8 +101,11 @@ struct SweepArgs {
     const void *mtab;             // Real[MT_ROWS][Nv]: unit wall Maxwellians, free stream
     int side_inflow[6];           // domain side s is a free-stream boundary
     void *FX, *FY, *FZ;           // face planes: [nz*ny][Nv], [nz*nx][Nv], [ny*nx][Nv]
-    void *part;                   // [n_vg][ncell][NPART]: double (FP64 path) or float2 (s, c)
-                                  // with value s - c (FP32 path, Kahan pair)
+    void *part;                   // staged sweep: [n_vg][ncell][NPART], double (FP64 path) or
+                                  // float2 (s, c) with value s - c (FP32 path, Kahan pair)
+    void *acc;                    // persistent sweep: [nacc][ncell][NACC] ordered accumulators
+    int nacc;                     // accumulators: velocity group g of an octant adds into g % nacc
+    int *tok;                     // persistent sweep: [nacc][nbz][nby][nbx] chain tokens
     unsigned long long ncell;
     int line16;                   // every octant has x-lines of 16 nodes (specialised moment loop)
     int uniform;                  // equal cell widths along each axis: a_d is per velocity
@@ -93,10 +123,16 @@ struct BatchSweepArgs {
     int *counter;                 // claim counter, zero at launch
     int *flags;                   // completion flags, zero at launch
     const int *flag_off;          // [n_inst] first flag of each instance
+    const int *pos;               // [n_items] place of each item in its accumulator chain
+    void *scratch;                // [grid][bz * SLICE][NPART] per-CTA moment partials
+    unsigned long long scratch_stride;  // bytes of one CTA's scratch, sweep_scratch_bytes(bz)
     int *error;                   // set to 1 when a bounded wait gives up
     long long spin_limit;         // polls before a wait gives up
     int skip_publish;             // fault injection: this item never sets its flag (-1: none)
 };
+// Bytes of one CTA's scratch partials for blocks bz cells deep (both precisions
+// store 8 bytes per slot).
+inline size_t sweep_scratch_bytes(int bz) { return (size_t)bz * SLICE * NPART * 8; }
 
 // Cell flags travel in the coefficient array as the bit pattern of a Real
 // (no conversion instruction on either side).
@@ -142,15 +178,27 @@ int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, s
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s);
 size_t sweep_smem_bytes(int precision, int tv, int line16, int nxo_max);
 
-struct CloseArgs {
-    int nx, ny, nz;
+// Per-cell sums of the staged sweep's per-group partials (fixed group order).
+struct PartSumArgs {
     unsigned long long ncell;
     int n_vg;
     const int *vg_oct;            // [n_vg] octant of each velocity group
     const void *part;             // [n_vg][ncell][NPART], see SweepArgs::part
+    int precision;
+    const uint8_t *solid;         // [ncell] or NULL
+    double *sums;                 // [NSUM][ncell]
+    const void *coef;             // sweep-precision coefficients (U centre)
+    const int8_t *wall_kind;      // [6][ncell]
+    RefMoments ref;               // moments of the reference Maxwellian, added to every cell
+};
+
+struct ClosureArgs {
+    int nx, ny, nz;
+    unsigned long long ncell;
+    const double *sums;           // [NSUM][ncell]
     const void *coef;             // sweep-precision coefficients (U centre)
     int precision;
-    const double *mac;            // [8][ncell] step n
+    int q_lagged;                 // 1: q = S3 / 2 about the lagged U^n (no shift)
     double *mac_new;              // [8][ncell] step n+1 (before rescale)
     double *rho_w_new;            // [6][ncell]
     const int8_t *wall_kind;      // [6][ncell]: -1 not a wall, 0..6 wall kind
@@ -167,7 +215,21 @@ cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, 
 // values.
 constexpr int CLOSE_CELLS = 32;
 inline size_t close_blocks(size_t ncell) { return (ncell + CLOSE_CELLS - 1) / CLOSE_CELLS; }
-cudaError_t launch_close(const CloseArgs &a, cudaStream_t s);
+cudaError_t launch_part_sums(const PartSumArgs &a, cudaStream_t s);
+// Per-cell sums of the persistent sweep's ordered accumulators (fixed order).
+struct AccSumArgs {
+    int precision;
+    const void *acc;
+    int nacc;
+    unsigned long long ncell;
+    const uint8_t *solid;         // [ncell] or NULL
+    double *sums;                 // [NSUM][ncell]
+    const void *coef;             // sweep-precision coefficients (U centre)
+    const int8_t *wall_kind;      // [6][ncell]
+    RefMoments ref;
+};
+cudaError_t launch_acc_sums(const AccSumArgs &a, cudaStream_t s);
+cudaError_t launch_closure(const ClosureArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_mass(const double *blk_mass, int n_blocks, double M0, int rescale, double *scale,
                                  cudaStream_t s);
 cudaError_t launch_scale_residual(double *mac_new, double *rho_w_new, const double *mac, const uint8_t *solid,

@@ -80,7 +80,6 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
 
     Carve cv;
     const size_t o_coef = cv.take(n * NCOEF * rsz);
-    const size_t o_vel64 = cv.take(t.vel64.size() * sizeof(double));
     const size_t o_vel = cv.take(t.vel64.size() * rsz);
     const size_t o_velm = cv.take((size_t)t.Nv * 8 * rsz);
     const size_t o_mt = cv.take(t.mt.size() * rsz);
@@ -88,6 +87,7 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
                  fz_bytes = (size_t)t.ny * t.nx * t.Nv * rsz;
     const size_t o_fx = cv.take(fx_bytes), o_fy = cv.take(fy_bytes), o_fz = cv.take(fz_bytes);
     const size_t o_part = cv.take((size_t)t.n_vg * NPART * n * 8);
+    const size_t o_sums = cv.take((size_t)NSUM * n * sizeof(double));
     const size_t o_rdx = cv.take(t.nx * sizeof(double)), o_rdy = cv.take(t.ny * sizeof(double)),
                  o_rdz = cv.take(t.nz * sizeof(double));
     const size_t o_dx = cv.take(t.nx * sizeof(double)), o_dy = cv.take(t.ny * sizeof(double)),
@@ -125,7 +125,7 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
         oct[8 + o] = t.oct_vcount[o];
         oct[16 + o] = t.oct_vgbase[o];
     }
-    bool ok = put(o_vel64, t.vel64.data(), t.vel64.size() * sizeof(double)) && put_real(o_vel, t.vel64) &&
+    bool ok = put_real(o_vel, t.vel64) &&
               put_real(o_mt, t.mt) &&
               (rsz == sizeof(double) ? put(o_velm, t.velm64.data(), t.velm64.size() * sizeof(double))
                                      : put(o_velm, t.velm32.data(), t.velm32.size() * sizeof(float))) &&
@@ -152,7 +152,7 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
                     reinterpret_cast<double *>(b + o_rdy), reinterpret_cast<double *>(b + o_rdz), t.nx, t.ny, t.nz,
                     t.mu_ref, t.omega, t.Pr, coef, st) != cudaSuccess)
         return KGS_ECUDA;
-    SweepArgs a;
+    SweepArgs a{};
     a.nx = t.nx;
     a.ny = t.ny;
     a.nz = t.nz;
@@ -190,17 +190,26 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
         a.work = d_work + t.stage_off[s];
         if (launch_sweep(t.precision, t.tv, a, t.stage_n[s], t.max_vg, st) != cudaSuccess) return KGS_ECUDA;
     }
-    CloseArgs ca;
+    PartSumArgs pa;
+    pa.ncell = n;
+    pa.n_vg = t.n_vg;
+    pa.vg_oct = reinterpret_cast<const int *>(b + o_vgoct);
+    pa.part = b + o_part;
+    pa.precision = t.precision;
+    pa.solid = d_solid;
+    pa.sums = reinterpret_cast<double *>(b + o_sums);
+    pa.coef = coef;
+    pa.wall_kind = reinterpret_cast<const int8_t *>(b + o_kind);
+    pa.ref = t.ref;
+    ClosureArgs ca;
     ca.nx = t.nx;
     ca.ny = t.ny;
     ca.nz = t.nz;
     ca.ncell = n;
-    ca.n_vg = t.n_vg;
-    ca.vg_oct = reinterpret_cast<const int *>(b + o_vgoct);
-    ca.part = b + o_part;
+    ca.sums = pa.sums;
     ca.coef = coef;
     ca.precision = t.precision;
-    ca.mac = macros_in;
+    ca.q_lagged = 0;
     ca.mac_new = macros_out;
     ca.rho_w_new = rho_w_out;
     ca.wall_kind = reinterpret_cast<const int8_t *>(b + o_kind);
@@ -212,7 +221,7 @@ extern "C" int kgs_iterate_noalloc(const kgs_grid *grid, const uint8_t *solid, c
     ca.blk_mass = reinterpret_cast<double *>(b + o_bmass);
     double *d_scale = reinterpret_cast<double *>(b + o_scale);
     double *d_resid = reinterpret_cast<double *>(b + o_resid);
-    if (launch_close(ca, st) != cudaSuccess ||
+    if (launch_part_sums(pa, st) != cudaSuccess || launch_closure(ca, st) != cudaSuccess ||
         launch_finalize_mass(ca.blk_mass, (int)close_blocks(n), M0, M0 > 0.0 ? 1 : 0, d_scale, st) != cudaSuccess ||
         launch_scale_residual(macros_out, rho_w_out, macros_in, d_solid, n, d_scale,
                               reinterpret_cast<double *>(b + o_bres), reinterpret_cast<int *>(b + o_bbad), n_red,

@@ -166,6 +166,9 @@ SweepArgs kgs::ctx_sweep_args(const kgs_ctx *c)
     a.FY = c->FY;
     a.FZ = c->FZ;
     a.part = c->part;
+    a.acc = c->acc;
+    a.nacc = t.nacc;
+    a.tok = c->p_tok;
     a.ncell = t.ncell;
     a.line16 = 1;
     for (int o = 0; o < 8; o++)
@@ -195,6 +198,7 @@ int kgs::ctx_launch_stages(kgs_ctx *c)
         KGS_CHECK(cudaMemcpyAsync(c->p_args, c->h_args, sizeof(SweepArgs), cudaMemcpyHostToDevice, st));
         KGS_CHECK(cudaMemsetAsync(c->p_counter, 0, sizeof(int), st));
         KGS_CHECK(cudaMemsetAsync(c->p_flags, 0, c->p_n_flags * sizeof(int), st));
+        KGS_CHECK(cudaMemsetAsync(c->p_tok, 0, ctx_n_tokens(t) * sizeof(int), st));
         BatchSweepArgs ba;
         ba.inst = c->p_args;
         ba.items = c->p_items;
@@ -202,6 +206,9 @@ int kgs::ctx_launch_stages(kgs_ctx *c)
         ba.counter = c->p_counter;
         ba.flags = c->p_flags;
         ba.flag_off = c->p_flag_off;
+        ba.pos = c->p_pos;
+        ba.scratch = c->p_scratch;
+        ba.scratch_stride = c->scratch_stride;
         ba.error = reinterpret_cast<int *>(c->resid + 2);
         ba.spin_limit = c->spin_limit;
         ba.skip_publish = -1;
@@ -239,6 +246,39 @@ void kgs::ctx_stage_items(const HostTables &t, int inst, int stage, std::vector<
     }
 }
 
+void kgs::chain_positions(const std::vector<int4> &items, const std::vector<const HostTables *> &tabs,
+                          std::vector<int> &pos)
+{
+    std::vector<std::vector<int>> count(tabs.size());
+    for (size_t i = 0; i < tabs.size(); i++) count[i].assign(ctx_n_tokens(*tabs[i]), 0);
+    pos.resize(items.size());
+    for (size_t it = 0; it < items.size(); it++) {
+        const int4 w = items[it];
+        const HostTables &t = *tabs[w.x];
+        const int o = w.y >> 24, vg = w.y & 0xffffff;
+        const int bxr = w.z & 1023, byr = (w.z >> 10) & 1023, bzr = (w.z >> 20) & 1023;
+        const int bx = (o & 1) ? bxr : t.nbx - 1 - bxr;
+        const int by = (o & 2) ? byr : t.nby - 1 - byr;
+        const int bz = (o & 4) ? bzr : t.nbz - 1 - bzr;
+        const size_t key = (((size_t)(vg % t.nacc) * t.nbz + bz) * t.nby + by) * t.nbx + bx;
+        pos[it] = count[w.x][key]++;
+    }
+}
+
+int kgs::ctx_alloc_acc(kgs_ctx *c)
+{
+    const HostTables &t = c->t;
+    const size_t bytes = (size_t)t.nacc * t.ncell * NACC * 8;
+    int rc = dalloc(c, &c->acc, bytes);
+    if (rc) return rc;
+    // every slot read by the sums is stored by the first item of its chain in
+    // every iteration; all-ones bytes (NaN in both precisions) make any slot
+    // that is not show up in the results at once
+    KGS_CHECK(cudaMemset(c->acc, 0xff, bytes));
+    c->use_acc = 1;
+    return KGS_OK;
+}
+
 int kgs::ctx_persist_init(kgs_ctx *c)
 {
     const HostTables &t = c->t;
@@ -247,37 +287,76 @@ int kgs::ctx_persist_init(kgs_ctx *c)
     const SweepArgs a = ctx_sweep_args(c);
     const int per_sm = sweep_persistent_occupancy(t.precision, t.tv, a.line16, a.uniform,
                                                   sweep_smem_bytes(t.precision, t.tv, a.line16, t.nxo_max));
-    if (per_sm < 1) return KGS_OK;  // keep the launch per stage
+    if (per_sm < 1) {
+        // the launch per stage, with per-group partials
+        return dalloc(c, &c->part, (size_t)t.n_vg * NPART * t.ncell * 8);
+    }
     std::vector<int4> items;
     for (int s = 0; s < (int)t.stage_n.size(); s++) ctx_stage_items(t, 0, s, items);
+    std::vector<int> pos;
+    chain_positions(items, std::vector<const HostTables *>(1, &t), pos);
     int rc;
     c->p_n_flags = (size_t)t.n_vg * t.nbx * t.nby * t.nbz;
-    if ((rc = upload(c, &c->p_items, items)) || (rc = dalloc_t(c, &c->p_counter, 1)) ||
-        (rc = dalloc_t(c, &c->p_flags, c->p_n_flags)) || (rc = upload(c, &c->p_flag_off, std::vector<int>(1, 0))) ||
-        (rc = dalloc_t(c, &c->p_args, 1)))
+    c->persist_grid = sms * per_sm;
+    c->scratch_stride = sweep_scratch_bytes(t.bz);
+    if ((rc = upload(c, &c->p_items, items)) || (rc = upload(c, &c->p_pos, pos)) ||
+        (rc = dalloc_t(c, &c->p_counter, 1)) || (rc = dalloc_t(c, &c->p_flags, c->p_n_flags)) ||
+        (rc = dalloc_t(c, &c->p_tok, ctx_n_tokens(t))) ||
+        (rc = upload(c, &c->p_flag_off, std::vector<int>(1, 0))) || (rc = dalloc_t(c, &c->p_args, 1)) ||
+        (rc = dalloc(c, &c->p_scratch, (size_t)c->persist_grid * c->scratch_stride)) || (rc = ctx_alloc_acc(c)))
         return rc;
     KGS_CHECK(cudaMallocHost(&c->h_args, sizeof(SweepArgs)));
     c->persist_items = (int)items.size();
-    c->persist_grid = sms * per_sm;
     c->persist = 1;
     return KGS_OK;
 }
 
-int kgs::ctx_launch_closure(kgs_ctx *c, double *resid_dev)
+int kgs::ctx_launch_sums(kgs_ctx *c)
+{
+    const HostTables &t = c->t;
+    if (c->use_acc) {
+        AccSumArgs aa;
+        aa.precision = t.precision;
+        aa.acc = c->acc;
+        aa.nacc = t.nacc;
+        aa.ncell = t.ncell;
+        aa.solid = c->solid;
+        aa.sums = c->sums;
+        aa.coef = c->coef;
+        aa.wall_kind = c->wall_kind;
+        aa.ref = t.ref;
+        KGS_CHECK(launch_acc_sums(aa, c->stream));
+    } else {
+        PartSumArgs pa;
+        pa.ncell = t.ncell;
+        pa.n_vg = t.n_vg;
+        pa.vg_oct = c->d_vg_oct;
+        pa.part = c->part;
+        pa.precision = t.precision;
+        pa.solid = c->solid;
+        pa.sums = c->sums;
+        pa.coef = c->coef;
+        pa.wall_kind = c->wall_kind;
+        pa.ref = t.ref;
+        KGS_CHECK(launch_part_sums(pa, c->stream));
+    }
+    c->kernel_launches += 1;
+    return KGS_OK;
+}
+
+int kgs::ctx_launch_closure(kgs_ctx *c, double *resid_dev, const double *sums)
 {
     const HostTables &t = c->t;
     cudaStream_t st = c->stream;
-    CloseArgs ca;
+    ClosureArgs ca;
     ca.nx = t.nx;
     ca.ny = t.ny;
     ca.nz = t.nz;
     ca.ncell = t.ncell;
-    ca.n_vg = t.n_vg;
-    ca.vg_oct = c->d_vg_oct;
-    ca.part = c->part;
+    ca.sums = sums ? sums : c->sums;
     ca.coef = c->coef;
     ca.precision = t.precision;
-    ca.mac = c->mac;
+    ca.q_lagged = c->q_lagged;
     ca.mac_new = c->mac_new;
     ca.rho_w_new = c->rho_w_new;
     ca.wall_kind = c->wall_kind;
@@ -287,7 +366,7 @@ int kgs::ctx_launch_closure(kgs_ctx *c, double *resid_dev)
     ca.dz = c->ddz;
     ca.solid = c->solid;
     ca.blk_mass = c->blk_mass;
-    KGS_CHECK(launch_close(ca, st));
+    KGS_CHECK(launch_closure(ca, st));
     KGS_CHECK(launch_finalize_mass(c->blk_mass, (int)close_blocks(t.ncell), c->M0, c->mass_rescale, c->scale, st));
     KGS_CHECK(launch_scale_residual(c->mac_new, c->rho_w_new, c->mac, c->solid, t.ncell, c->scale, c->blk_res,
                                     c->blk_bad, c->n_red_blocks, st));
@@ -309,7 +388,8 @@ namespace {
 int run_iteration(kgs_ctx *c, double *residual, int *bad)
 {
     int rc;
-    if ((rc = ctx_launch_coef(c)) || (rc = ctx_launch_stages(c)) || (rc = ctx_launch_closure(c, c->resid)))
+    if ((rc = ctx_launch_coef(c)) || (rc = ctx_launch_stages(c)) || (rc = ctx_launch_sums(c)) ||
+        (rc = ctx_launch_closure(c, c->resid, nullptr)))
         return rc;
     KGS_CHECK(cudaMemcpyAsync(c->h_resid, c->resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
@@ -359,7 +439,7 @@ int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const k
     if (!out || !opts) return KGS_EINVAL;
     *out = nullptr;
     int rc = validate_problem(grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta,
-                              opts->block_z);
+                              opts->block_z, opts->vz_begin, opts->vz_end);
     if (rc) return rc;
     (void)cudaGetLastError();  // launches below check their own status
     if ((rc = ctx_create(out, grid, solid, vg, gas, bc, opts))) return rc;
@@ -391,7 +471,9 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
     c->max_iters = opts->max_iters > 0 ? opts->max_iters : 1000;
     c->tol = opts->tol > 0.0 ? opts->tol : 1e-8;
     HostTables &t = c->t;
-    build_tables(t, grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta, opts->block_z);
+    build_tables(t, grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta, opts->block_z,
+                 opts->vz_begin, opts->vz_end);
+    c->q_lagged = opts->q_lagged ? 1 : 0;
     const size_t n = t.ncell;
     const size_t rsz = t.real_bytes();
     c->n_red_blocks = (int)((n + 255) / 256);
@@ -402,7 +484,7 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
         (rc = dalloc(c, &c->FX, (size_t)t.nz * t.ny * t.Nv * rsz)) ||
         (rc = dalloc(c, &c->FY, (size_t)t.nz * t.nx * t.Nv * rsz)) ||
         (rc = dalloc(c, &c->FZ, (size_t)t.ny * t.nx * t.Nv * rsz)) ||
-        (rc = dalloc(c, &c->part, (size_t)t.n_vg * NPART * n * 8)) || (rc = upload(c, &c->rdx, t.rdx)) ||
+        (rc = dalloc_t(c, &c->sums, (size_t)NSUM * n)) || (rc = upload(c, &c->rdx, t.rdx)) ||
         (rc = upload(c, &c->rdy, t.rdy)) || (rc = upload(c, &c->rdz, t.rdz)) || (rc = upload(c, &c->ddx, t.dx)) ||
         (rc = upload(c, &c->ddy, t.dy)) || (rc = upload(c, &c->ddz, t.dz)) ||
         (rc = upload(c, &c->side_flags, t.side_flags)) || (rc = upload(c, &c->wall_kind, t.wall_kind)) ||
@@ -469,6 +551,43 @@ int kgs_iterate(kgs_ctx *c, int n_iters, int *done, double *residual)
     if (done) *done = count;
     if (residual) *residual = r;
     return rc;
+}
+
+int kgs_sweep_sums(kgs_ctx *c, double *sums_dev)
+{
+    if (!c || !sums_dev) return KGS_EINVAL;
+    if (cudaSetDevice(c->dev) != cudaSuccess) return KGS_ECUDA;
+    (void)cudaGetLastError();  // launches below check their own status
+    int rc;
+    if ((rc = ctx_launch_coef(c)) || (rc = ctx_launch_stages(c)) || (rc = ctx_launch_sums(c))) return rc;
+    KGS_CHECK(cudaMemcpyAsync(sums_dev, c->sums, sizeof(double) * NSUM * c->t.ncell, cudaMemcpyDeviceToDevice,
+                              c->stream));
+    KGS_CHECK(cudaMemcpyAsync(c->h_resid, c->resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    KGS_CHECK(cudaStreamSynchronize(c->stream));
+    if (c->persist && *reinterpret_cast<const int *>(c->h_resid + 2) != 0) {
+        KGS_CHECK(cudaMemsetAsync(c->resid + 2, 0, sizeof(double), c->stream));
+        KGS_CHECK(cudaStreamSynchronize(c->stream));
+        return KGS_ETIMEOUT;
+    }
+    return KGS_OK;
+}
+
+int kgs_close_sums(kgs_ctx *c, const double *sums_dev, double *residual)
+{
+    if (!c || !sums_dev) return KGS_EINVAL;
+    if (cudaSetDevice(c->dev) != cudaSuccess) return KGS_ECUDA;
+    (void)cudaGetLastError();
+    // the closure takes the lagged velocity centre from the coefficients of
+    // this iteration, which kgs_sweep_sums computed
+    int rc;
+    if ((rc = ctx_launch_closure(c, c->resid, sums_dev))) return rc;
+    KGS_CHECK(cudaMemcpyAsync(c->h_resid, c->resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    KGS_CHECK(cudaStreamSynchronize(c->stream));
+    const double r = c->h_resid[0];
+    const bool bad = c->h_resid[1] != 0.0;
+    ctx_finish(c, r);
+    if (residual) *residual = r;
+    return bad ? KGS_EDIVERGED : KGS_OK;
 }
 
 int kgs_moments(kgs_ctx *c, double *out)

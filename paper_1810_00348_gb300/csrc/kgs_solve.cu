@@ -19,11 +19,11 @@
 
 namespace {
 
-constexpr int CHUNK = 5;             // mixed iterations between progress checks
-constexpr int PATIENCE = 2;          // checks without progress before the switch ...
-constexpr double NEAR_FLOOR = 1e-3;  // ... once the residual is below this
-constexpr int PATIENCE_FAR = 20;     // checks without progress above it (a transient that does not end)
-constexpr double PROGRESS = 0.9;     // progress: residual below 0.9 x the best so far
+using kgs::SOLVE_CHUNK;
+using kgs::SOLVE_NEAR_FLOOR;
+using kgs::SOLVE_PATIENCE;
+using kgs::SOLVE_PATIENCE_FAR;
+using kgs::SOLVE_PROGRESS;
 
 kgs_opts opts_for(const kgs_problem *p, int precision, double tol, int max_iters, void *stream)
 {
@@ -31,6 +31,7 @@ kgs_opts opts_for(const kgs_problem *p, int precision, double tol, int max_iters
     o.precision = precision;
     o.wall_norm = p->wall_norm;
     o.mass_rescale = p->mass_rescale;
+    o.q_lagged = p->q_lagged;
     o.max_iters = max_iters;
     o.tol = tol;
     o.stream = stream;
@@ -63,13 +64,13 @@ extern "C" int kgs_solve(const kgs_problem *p, const double *initial, double tol
     int stalled = 0;
     while (n_mixed < max_iters) {
         int done = 0;
-        rc = kgs_iterate(m, std::min(CHUNK, max_iters - n_mixed), &done, &r);
+        rc = kgs_iterate(m, std::min(SOLVE_CHUNK, max_iters - n_mixed), &done, &r);
         n_mixed += done;
         if (rc) return finish(rc);
         if (r < tol) break;
-        if (r < PROGRESS * best) {
+        if (r < SOLVE_PROGRESS * best) {
             stalled = 0;
-        } else if (++stalled >= (r < NEAR_FLOOR ? PATIENCE : PATIENCE_FAR)) {
+        } else if (++stalled >= (r < SOLVE_NEAR_FLOOR ? SOLVE_PATIENCE : SOLVE_PATIENCE_FAR)) {
             break;
         }
         best = std::min(best, r);

@@ -45,6 +45,10 @@
 // global memory indexed by the cell position on the face: a block reads the
 // plane entries written by its upwind neighbour in the previous stage before
 // overwriting them with its own outflow.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "kgs_internal.h"
 
 namespace kgs {
@@ -196,8 +200,14 @@ __device__ __forceinline__ Real ld_face(const Real *p)
 
 // One work item: block w = (octant, reflected block coordinates) and
 // velocity group vgy of that octant.  Called by every thread of the CTA.
+//
+// The item's moment partials go, per (group, cell), to a.part (staged sweep,
+// COHERENT false) or, in the persistent sweep, to this CTA's scratch block
+// [bz * SLICE][NPART] indexed by the cell's place in the block, from where
+// chain_add moves them into the ordered accumulators.
 template <typename Real, int TV, int LINE, bool COHERENT, bool UNIF>
-__device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, const int vgy, unsigned char *smem)
+__device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, const int vgy, unsigned char *smem,
+                                           void *scratch)
 {
     using L = SmemLayout<Real, TV>;
     constexpr int VG = L::VG;
@@ -254,7 +264,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
     Real *FZp = static_cast<Real *>(a.FZ);
 
     // ---- per-thread velocities (vl = t + m*NT) and the moment-phase tables ----
-    Real xi[TV][3], axi[TV][3], mgx[TV], mgy[TV], mgz[TV], msol[TV];
+    // The FP32 sweep carries g = f - M_ref (mref: the reference Maxwellian of
+    // the velocity); every ghost value enters as ghost - M_ref and the source
+    // as f^S/tau - M_ref/tau.  The FP64 sweep carries f (mref unused).
+    Real xi[TV][3], axi[TV][3], mgx[TV], mgy[TV], mgz[TV], msol[TV], mref[TV];
     size_t gv[TV];
     bool ok[TV];
     const int rowx = a.side_inflow[sidex] ? MT_INFLOW : sidex;
@@ -285,7 +298,15 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         mgy[m] = mt[(size_t)rowy * Nv + gv[m]];
         mgz[m] = mt[(size_t)rowz * Nv + gv[m]];
         msol[m] = mt[(size_t)MT_SOLID * Nv + gv[m]];
+        mref[m] = sizeof(Real) == 4 ? velm[gv[m] * 8 + 5] : Real(0);
     }
+    // ghost value rho_w * (unit wall or free-stream Maxwellian), as carried
+    auto ghost = [&](Real rw, Real mg, int m) -> Real {
+        if constexpr (sizeof(Real) == 4)
+            return fma(rw, mg, -mref[m]);
+        else
+            return rw * mg;
+    };
     // |xi|^2 of each velocity, rounded once from its FP64 value
     Real xsq[TV];
 #pragma unroll
@@ -341,7 +362,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 if (lj2 >= ey) break;
                 const Real rw = wall_rho(sidex, CELL(GX(0), GY(lj2), z));
 #pragma unroll
-                for (int m = 0; m < TV; m++) phx[lj2][m] = rw * mgx[m];
+                for (int m = 0; m < TV; m++) phx[lj2][m] = ghost(rw, mgx[m], m);
             }
         } else {
             const Real *fi = FXp + ((size_t)z * ny + GY(0)) * Nv;
@@ -360,7 +381,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 if (li2 >= ex) break;
                 const Real rw = wall_rho(sidey, CELL(GX(li2), GY(0), z));
 #pragma unroll
-                for (int m = 0; m < TV; m++) phy[li2][m] = rw * mgy[m];
+                for (int m = 0; m < TV; m++) phy[li2][m] = ghost(rw, mgy[m], m);
             }
         } else {
             const Real *fi = FYp + ((size_t)z * nx + GX(0)) * Nv;
@@ -385,7 +406,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 const Real rw = wall_rho(sidez, CELL(GX(li), GY(lj), GZ(0)));
 #pragma unroll
                 for (int m = 0; m < TV; m++)
-                    if (ok[m]) slice[SL(li, lj) + t + m * NT] = rw * mgz[m];
+                    if (ok[m]) slice[SL(li, lj) + t + m * NT] = ghost(rw, mgz[m], m);
             }
     } else {
         const long long sx = px ? (long long)Nv : -(long long)Nv;
@@ -484,9 +505,9 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                             Real fy = slice[sidx - (BX + 1) * CS + vl];
                             Real fx = slice[sidx - CS + vl];
                             if (any_solid) {
-                                if (sol_x) fx = rwx * msol[m];
-                                if (sol_y) fy = rwy * msol[m];
-                                if (sol_z) fz = rwz * msol[m];
+                                if (sol_x) fx = ghost(rwx, msol[m], m);
+                                if (sol_y) fy = ghost(rwy, msol[m], m);
+                                if (sol_z) fz = ghost(rwz, msol[m], m);
                             }
                             // |c|^2 - |U|^2 = |xi|^2 - 2 U.xi and c.q' = xi.q' - U.q'
                             const Real s = fma(xi[m][0], m2ux, fma(xi[m][1], m2uy, fma(xi[m][2], m2uz, xsq[m])));
@@ -509,8 +530,23 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                                 az = axi[m][2] * rdz;
                                 den = rtau + ax + ay + az;
                             }
-                            const Real num = src + ax * fx + ay * fy + az * fz;
-                            const Real f = implicit_div(num, den);
+                            Real f;
+                            if constexpr (sizeof(Real) == 4) {
+                                // The same solution of Eq. (7) written about the upwind x value:
+                                //   f = f_x + (src - f_x/tau + a_y (f_y - f_x) + a_z (f_z - f_x)) / den.
+                                // On a smooth field the increment is small, so the one rounding
+                                // that matters is the final addition, which is unbiased.  The
+                                // plain form num * (1/den) scales f by the same rounding error of
+                                // 1/den in every cell of a velocity's characteristic, and that
+                                // error adds up along the sweep.
+                                Real t = fma(-rtau, fx + mref[m], src);
+                                t = fma(ay, fy - fx, t);
+                                t = fma(az, fz - fx, t);
+                                f = fma(t, rcp_approx(den), fx);
+                                (void)ax;
+                            } else {
+                                f = implicit_div(src + ax * fx + ay * fy + az * fz, den);
+                            }
                             if (ok[m]) slice[sidx + vl] = f;
                         }
                     }
@@ -749,7 +785,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
             __syncthreads();
             if (vp == 0 && valid) {
                 // the cell's NPART partials are contiguous (128 bytes)
-                Out *pp = static_cast<Out *>(a.part) + ((size_t)vgid * ncell + CELL(GX(li), GY(lj), z)) * NPART;
+                Out *pp = COHERENT ? static_cast<Out *>(scratch) + ((size_t)lk * SLICE + cl) * NPART
+                                   : static_cast<Out *>(a.part) + ((size_t)vgid * ncell + CELL(GX(li), GY(lj), z)) * NPART;
 #pragma unroll
                 for (int q = 0; q < NPART; q += 2) {
                     if constexpr (sizeof(Real) == 8) {
@@ -786,7 +823,7 @@ template <typename Real, int TV, int LINE, bool UNIF>
 __global__ void __launch_bounds__(NT, 2) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    sweep_item<Real, TV, LINE, false, UNIF>(a, a.work[blockIdx.x], blockIdx.y, smem);
+    sweep_item<Real, TV, LINE, false, UNIF>(a, a.work[blockIdx.x], blockIdx.y, smem, nullptr);
 }
 
 __device__ __forceinline__ int ld_acquire(const int *p)
@@ -812,10 +849,83 @@ __device__ bool wait_flag(const int *p, long long limit)
     return false;
 }
 
+// Bounded wait for a chain token to reach `v` (tokens only grow).
+__device__ bool wait_token(const int *p, int v, long long limit)
+{
+    for (long long i = 0; i < limit; i++) {
+        if (ld_acquire(p) >= v) return true;
+        __nanosleep(100);
+    }
+    return false;
+}
+
+// Ordered accumulation of one item's moment partials.  Velocity group g of
+// an octant adds into accumulator k = g % nacc; the items of one (k, block)
+// form a chain in the order they were claimed, and the item at place `pos`
+// adds after the one at pos - 1 (the first one stores).  The order is fixed
+// by the work list, so the sums are bit-reproducible, and no item waits for
+// one claimed after it.  The flux slots of the item (incoming flux onto the
+// wall ahead of its octant along x, y, z) go to the slots of those sides.
+// FP32 partials are Kahan pairs (s, c) with value s - c; the accumulator holds
+// a float-float pair (hi, lo) with value hi + lo, hi updated by a two-sum.
+template <typename Real>
+__device__ void chain_add(const SweepArgs &a, int o, int bxr, int byr, int bzr, int vg, int pos,
+                          const void *scratch)
+{
+    using Out = typename PartOut<Real>::T;
+    const bool px = (o & 1) != 0, py = (o & 2) != 0, pz = (o & 4) != 0;
+    const int bxi = px ? bxr : a.nbx - 1 - bxr;
+    const int byi = py ? byr : a.nby - 1 - byr;
+    const int bzi = pz ? bzr : a.nbz - 1 - bzr;
+    const int x0 = bxi * BX, ex = min(BX, a.nx - x0);
+    const int y0 = byi * BY, ey = min(BY, a.ny - y0);
+    const int z0 = bzi * a.bz, ez = min(a.bz, a.nz - z0);
+    const size_t ncell = a.ncell;
+    const Out *sc = static_cast<const Out *>(scratch);
+    Out *acc = static_cast<Out *>(a.acc) + (size_t)(vg % a.nacc) * ncell * NACC;
+    const int n = ez * SLICE * NPART;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < n; e += NT) {
+        const int q = e % NPART, cl = (e / NPART) % SLICE, lk = e / (NPART * SLICE);
+        const int li = cl % BX, lj = cl / BX;
+        if (li >= ex || lj >= ey) continue;
+        const int x = px ? x0 + li : x0 + ex - 1 - li;
+        const int y = py ? y0 + lj : y0 + ey - 1 - lj;
+        const int z = pz ? z0 + lk : z0 + ez - 1 - lk;
+        const size_t cell = (size_t)x + (size_t)a.nx * ((size_t)y + (size_t)a.ny * z);
+        const int slot = q < P_FX ? q : SUM_F0 + 2 * (q - P_FX) + ((o >> (q - P_FX)) & 1);
+        const Out v = sc[e];  // written by this CTA: the same L1 path
+        Out *dst = acc + cell * NACC + slot;
+        if (pos == 0 && q >= P_FX) {
+            // the first item of the chain stores every slot: the flux onto the
+            // wall behind its octant is zero
+            Out *other = acc + cell * NACC + (SUM_F0 + 2 * (q - P_FX) + 1 - ((o >> (q - P_FX)) & 1));
+            if constexpr (sizeof(Real) == 8)
+                *other = 0.0;
+            else
+                *other = make_float2(0.f, 0.f);
+        }
+        if constexpr (sizeof(Real) == 8) {
+            *dst = pos == 0 ? v : __ldcg(dst) + v;
+        } else {
+            if (pos == 0) {
+                *dst = make_float2(v.x, -v.y);
+            } else {
+                const float2 cur = __ldcg(dst);
+                const float t = cur.x + v.x;
+                const float bp = t - cur.x;
+                const float err = (cur.x - (t - bp)) + (v.x - bp);
+                *dst = make_float2(t, cur.y + (err - v.y));
+            }
+        }
+    }
+}
+
 // Persistent sweep over the items of many problem instances.  Items are
 // claimed in list order (stage-major), so every item's upwind dependencies
-// were claimed earlier by CTAs that are running: the waits always end unless
-// an error stopped a producer, and then they end at the poll limit.
+// and its accumulator-chain predecessor were claimed earlier by CTAs that are
+// running: the waits always end unless an error stopped a producer, and then
+// they end at the poll limit.
 template <typename Real, int TV, int LINE, bool UNIF>
 __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSweepArgs b)
 {
@@ -850,28 +960,64 @@ __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSwee
         }
         __syncthreads();
         if (!s_go) break;
-        sweep_item<Real, TV, LINE, true, UNIF>(sa, make_int4(o, bxr, byr, bzr), vg, smem);
+        void *scratch = static_cast<unsigned char *>(b.scratch) + (size_t)blockIdx.x * b.scratch_stride;
+        sweep_item<Real, TV, LINE, true, UNIF>(sa, make_int4(o, bxr, byr, bzr), vg, smem, scratch);
         __syncthreads();
+        // the downwind blocks may start: the face planes are written
         if (threadIdx.x == 0 && it != b.skip_publish) {
             __threadfence();
             const int vgg = item.w;
             st_release(fl + ((vgg * sa.nbz + bzr) * sa.nby + byr) * sa.nbx + bxr, 1);
         }
+        // then the item's turn in its accumulator chain
+        const int pos = b.pos[it];
+        const int bxi = (o & 1) ? bxr : sa.nbx - 1 - bxr;
+        const int byi = (o & 2) ? byr : sa.nby - 1 - byr;
+        const int bzi = (o & 4) ? bzr : sa.nbz - 1 - bzr;
+        int *tk = sa.tok + (((size_t)(vg % sa.nacc) * sa.nbz + bzi) * sa.nby + byi) * sa.nbx + bxi;
+        if (threadIdx.x == 0) {
+            bool ok = pos == 0 || wait_token(tk, pos, b.spin_limit);
+            if (!ok) atomicExch(b.error, 1);
+            s_go = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        chain_add<Real>(sa, o, bxr, byr, bzr, vg, pos, scratch);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(tk, pos + 1);
+        }
     }
+}
+
+// The dynamic shared-memory limit is an attribute of a kernel on one device:
+// it is raised (never lowered) on the current device before a launch that
+// needs more than that device has been given, under a lock so that host
+// threads launching the same kernel do not undo each other's setting.
+std::mutex g_smem_mutex;
+std::map<std::pair<int, const void *>, size_t> g_smem_set;
+
+cudaError_t ensure_smem(const void *fn, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    size_t &have = g_smem_set[std::make_pair(dev, fn)];
+    if (bytes <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 
 template <typename Real, int TV, int LINE, bool UNIF>
 cudaError_t launch_t(const SweepArgs &a, int n_items, int max_vg, cudaStream_t s)
 {
     using L = SmemLayout<Real, TV>;
-    static size_t configured = 0;
     const size_t bytes = L::total(a.nxo_max, LINE > 0);
-    if (bytes > configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_kernel<Real, TV, LINE, UNIF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        configured = bytes;
-    }
+    cudaError_t e = ensure_smem(reinterpret_cast<const void *>(sweep_kernel<Real, TV, LINE, UNIF>), bytes);
+    if (e != cudaSuccess) return e;
     dim3 grid(n_items, max_vg);
     sweep_kernel<Real, TV, LINE, UNIF><<<grid, NT, bytes, s>>>(a);
     return cudaGetLastError();
@@ -891,14 +1037,10 @@ template <typename Real, int TV, int LINE, bool UNIF>
 cudaError_t launch_persistent_t(const BatchSweepArgs &b, int nxo_max, int grid, cudaStream_t s)
 {
     using L = SmemLayout<Real, TV>;
-    static size_t configured = 0;
     const size_t bytes = L::total(nxo_max, LINE > 0);
-    if (bytes > configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE, UNIF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        configured = bytes;
-    }
+    cudaError_t e =
+        ensure_smem(reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF>), bytes);
+    if (e != cudaSuccess) return e;
     sweep_persistent_kernel<Real, TV, LINE, UNIF><<<grid, NT, bytes, s>>>(b);
     return cudaGetLastError();
 }
@@ -907,8 +1049,8 @@ template <typename Real, int TV, int LINE, bool UNIF>
 int occupancy_t(size_t smem)
 {
     int n = 0;
-    if (cudaFuncSetAttribute(sweep_persistent_kernel<Real, TV, LINE, UNIF>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (ensure_smem(reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF>), smem) !=
+        cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }

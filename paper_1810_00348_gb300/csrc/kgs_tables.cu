@@ -18,7 +18,8 @@ double maxwellian(double rho, const double U[3], double T, const double xi[3])
 }  // namespace
 
 int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
-                     const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z)
+                     const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z, int vz_begin,
+                     int vz_end)
 {
     if (!grid || !vg || !gas || !bc) return KGS_EINVAL;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !grid->dx || !grid->dy || !grid->dz) return KGS_EINVAL;
@@ -30,6 +31,8 @@ int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid
     if (v_per_cta != 0 && v_per_cta != 128 && v_per_cta != 256) return KGS_EINVAL;
     if (precision == KGS_FP64 && v_per_cta == 256) return KGS_EINVAL;
     if (block_z < 0) return KGS_EINVAL;
+    if (!(vz_begin == 0 && vz_end == 0) && !(vz_begin >= 0 && vz_begin < vz_end && vz_end <= vg->nvz))
+        return KGS_EINVAL;
     const long long ncell = (long long)grid->nx * grid->ny * grid->nz;
     const long long nv = (long long)vg->nvx * vg->nvy * vg->nvz;
     if (ncell > (1LL << 31) || nv > (1LL << 24)) return KGS_EINVAL;
@@ -62,7 +65,8 @@ int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid
 }
 
 void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg,
-                  const kgs_gas *gas, const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z)
+                  const kgs_gas *gas, const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z,
+                  int vz_begin, int vz_end)
 {
     t.nx = grid->nx;
     t.ny = grid->ny;
@@ -71,7 +75,9 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
     t.nvx = vg->nvx;
     t.nvy = vg->nvy;
     t.nvz = vg->nvz;
-    t.Nv = t.nvx * t.nvy * t.nvz;
+    t.vz0 = vz_end > 0 ? vz_begin : 0;
+    t.vz1 = vz_end > 0 ? vz_end : t.nvz;
+    t.Nv = t.nvx * t.nvy * (t.vz1 - t.vz0);
     t.precision = precision;
     t.wall_norm_mode = wall_norm;
     // defaults measured on the 64^3 x 32^3 cavity: two velocities per thread
@@ -114,7 +120,7 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
     };
     for (int o = 0; o < 8; o++) {
         t.oct_vstart[o] = (int)order.size();
-        for (int iz = 0; iz < t.nvz; iz++)
+        for (int iz = t.vz0; iz < t.vz1; iz++)
             for (int iy = 0; iy < t.nvy; iy++)
                 for (int ix = 0; ix < t.nvx; ix++)
                     if (oct_of(ix, iy, iz) == o) order.push_back(ix + t.nvx * (iy + t.nvy * iz));
@@ -161,6 +167,12 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
         t.max_vg = std::max(t.max_vg, ng);
     }
     t.n_vg = (int)t.vg_oct.size();
+    // accumulators: velocity group g of an octant adds into g % nacc, and
+    // every accumulator must receive a group of every block, so nacc is at
+    // most the smallest group count of a non-empty octant
+    t.nacc = NACC_MAX;
+    for (int o = 0; o < 8; o++)
+        if (t.oct_vcount[o] > 0) t.nacc = std::min(t.nacc, (t.oct_vcount[o] + t.vg_size - 1) / t.vg_size);
 
     // ---- wall tables: kinds 0..5 domain sides, 6 solid surfaces ----
     double wallU[7][3], wallT[7];
@@ -177,17 +189,49 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
                 t.wall_norm[k * 6 + s] = std::sqrt(2.0 * M_PI / (R_GAS * wallT[k]));
                 continue;
             }
-            // discrete outgoing flux of the unit wall Maxwellian
+            // discrete outgoing flux of the unit wall Maxwellian, over every
+            // velocity of the grid (also when this context sweeps a part)
             const int d = s / 2;
             const double nrm = (s % 2) ? -1.0 : 1.0;
             double D = 0.0;
-            for (int g = 0; g < t.Nv; g++) {
-                const double *v = &t.vel64[g * 4];
-                const double xn = v[d] * nrm;
-                if (xn > 0.0) D += v[3] * xn * maxwellian(1.0, wallU[k], wallT[k], v);
-            }
+            for (int iz = 0; iz < t.nvz; iz++)
+                for (int iy = 0; iy < t.nvy; iy++)
+                    for (int ix = 0; ix < t.nvx; ix++) {
+                        const double v[3] = {vg->xi_x[ix], vg->xi_y[iy], vg->xi_z[iz]};
+                        const double xn = v[d] * nrm;
+                        if (xn > 0.0)
+                            D += vg->w_x[ix] * vg->w_y[iy] * vg->w_z[iz] * xn * maxwellian(1.0, wallU[k], wallT[k], v);
+                    }
             t.wall_norm[k * 6 + s] = D > 0.0 ? 1.0 / D : 0.0;
         }
+    // FP32 sweep: the reference Maxwellian is the uniform state the solve
+    // starts from (the free stream if a side is an inflow, else rho = 1,
+    // U = 0, T = 1); its FP32 values go into the velocity table and the
+    // moments of exactly those values, in FP64, into t.ref.  On the inflow
+    // faces the reference equals the ghost, so their deviation is zero.
+    t.ref = RefMoments{};
+    if (precision == KGS_MIXED) {
+        double refU[3] = {0.0, 0.0, 0.0}, refT = 1.0, refRho = 1.0;
+        if (t.any_inflow) {
+            refRho = bc->rho_in;
+            refT = bc->T_in;
+            for (int d = 0; d < 3; d++) refU[d] = bc->U_in[d];
+        }
+        for (int g = 0; g < t.Nv; g++) {
+            const double *v = &t.vel64[g * 4];
+            const float m32 = (float)maxwellian(refRho, refU, refT, v);
+            t.velm32[g * 8 + 5] = m32;
+            const double wm = v[3] * (double)m32;
+            for (int a = 0; a <= 3; a++)
+                for (int b = 0; a + b <= 3; b++)
+                    for (int c = 0; a + b + c <= 3; c++)
+                        t.ref.raw[ref_index(a, b, c)] += wm * std::pow(v[0], a) * std::pow(v[1], b) * std::pow(v[2], c);
+            for (int side = 0; side < 6; side++) {
+                const double xn = v[side / 2] * ((side % 2) ? -1.0 : 1.0);  // normal from the wall into the gas
+                if (xn < 0.0) t.ref.flux[side] += wm * (-xn);
+            }
+        }
+    }
     t.mt.assign((size_t)MT_ROWS * t.Nv, 0.0);
     for (int g = 0; g < t.Nv; g++) {
         const double *v = &t.vel64[g * 4];

@@ -14,7 +14,8 @@ namespace kgs {
 constexpr double R_GAS = 0.5;  // velocity unit sqrt(2 R T0)
 
 struct HostTables {
-    int nx = 0, ny = 0, nz = 0, nvx = 0, nvy = 0, nvz = 0, Nv = 0;
+    int nx = 0, ny = 0, nz = 0, nvx = 0, nvy = 0, nvz = 0, Nv = 0;  // Nv: velocities swept by this context
+    int vz0 = 0, vz1 = 0;                    // swept velocity planes iz in [vz0, vz1)
     size_t ncell = 0;
     long long n_fluid = 0;
     int precision = KGS_FP64, wall_norm_mode = KGS_WALL_DISCRETE;
@@ -26,12 +27,14 @@ struct HostTables {
     // velocities sorted by octant (bit d set: xi_d >= 0), ix fastest
     int oct_vstart[8] = {0}, oct_vcount[8] = {0}, oct_vgbase[8] = {0}, oct_nx[8] = {0};
     int n_vg = 0, max_vg = 0, nxo_max = 1;
+    int nacc = 1;                            // ordered accumulators of the persistent sweep
     std::vector<int> vg_oct;                 // octant of each velocity group
     std::vector<double> vel64;               // [Nv][4] xi_x, xi_y, xi_z, w
     std::vector<double> axis64;              // 1D nodes and weights: xi_x, xi_y, xi_z, w_x, w_y, w_z
     std::vector<double> velm64;              // [Nv][8] w_x, w_y w_z, 0 ...
     std::vector<float> velm32;               // [Nv][8] w_x, w_y w_z, low parts of xi
     std::vector<double> mt;                  // [MT_ROWS][Nv] wall Maxwellians, free stream
+    RefMoments ref{};                        // FP32 sweep: moments of the reference Maxwellian
     std::vector<double> wall_norm;           // [7][6] rho_w = F * wall_norm[kind][side]
     std::vector<int8_t> wall_kind;           // [6][ncell]
     std::vector<uint8_t> side_flags;         // [2][ncell]: solid-neighbour bits, wall-face bits
@@ -59,11 +62,15 @@ struct HostTables {
 };
 
 // Argument checks of kgs_setup (KGS_OK or KGS_EINVAL).
+// vz_begin, vz_end: the velocity planes iz in [vz_begin, vz_end) of a
+// velocity-space partition (0, 0: all of them).
 int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
-                     const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z);
+                     const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z, int vz_begin = 0,
+                     int vz_end = 0);
 
 // Build every host table of a validated problem.
 void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg,
-                  const kgs_gas *gas, const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z);
+                  const kgs_gas *gas, const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z,
+                  int vz_begin = 0, int vz_end = 0);
 
 }  // namespace kgs

@@ -56,7 +56,8 @@ class KgsBc(ctypes.Structure):
 class KgsOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("wall_norm", ctypes.c_int), ("mass_rescale", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("tol", ctypes.c_double), ("v_per_cta", ctypes.c_int),
-                ("block_z", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("block_z", ctypes.c_int), ("stream", ctypes.c_void_p), ("q_lagged", ctypes.c_int),
+                ("vz_begin", ctypes.c_int), ("vz_end", ctypes.c_int)]
 
 
 class KgsInfo(ctypes.Structure):
@@ -87,6 +88,8 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_longlong)]),
     "kgs_destroy": (None, [ctypes.c_void_p]),
     "kgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "kgs_sweep_sums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "kgs_close_sums": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _dp]),
     "kgs_iterate_noalloc": (ctypes.c_int, [ctypes.POINTER(KgsGrid), ctypes.POINTER(ctypes.c_uint8),
                                            ctypes.POINTER(KgsVgrid), ctypes.POINTER(KgsGas), ctypes.POINTER(KgsBc),
                                            ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
@@ -175,13 +178,16 @@ def _problem_structs(prob, keep):
     return g, v, gas, bc, solid_p
 
 
-def kgs_setup(prob, precision=KGS_FP64, max_iters=1000, tol=1e-8, v_per_cta=0, block_z=0, stream=None):
-    """kgs_setup for an ``inputs.Problem``; stream is a cudaStream_t value (int) or None."""
+def kgs_setup(prob, precision=KGS_FP64, max_iters=1000, tol=1e-8, v_per_cta=0, block_z=0, stream=None,
+              vz=(0, 0)):
+    """kgs_setup for an ``inputs.Problem``; stream is a cudaStream_t value (int) or None; vz = (begin, end)
+    sweeps only those velocity planes (a part of a velocity-space partition)."""
     lib = load()
     keep = []
     g, v, gas, bc, solid_p = _problem_structs(prob, keep)
     opts = KgsOpts(precision, int(prob.wall_mode), int(prob.mass_rescale), max_iters, tol, v_per_cta, block_z,
-                   ctypes.c_void_p(stream) if stream else None)
+                   ctypes.c_void_p(stream) if stream else None, int(getattr(prob, "q_lagged", 0)),
+                   int(vz[0]), int(vz[1]))
     h = ctypes.c_void_p()
     _check(lib.kgs_setup(ctypes.byref(h), ctypes.byref(g), solid_p, ctypes.byref(v), ctypes.byref(gas),
                          ctypes.byref(bc), ctypes.byref(opts)), "kgs_setup")
@@ -259,6 +265,21 @@ def kgs_profile(ctx):
     return ms.value, sl.value, kl.value
 
 
+def kgs_sweep_sums(ctx, sums_dev):
+    """One sweep of the context's velocities: per-cell sums [19][ncell] (FP64) written to the device
+    pointer sums_dev (int); the state does not change."""
+    return _check(load().kgs_sweep_sums(ctx.handle, ctypes.c_void_p(sums_dev)), "kgs_sweep_sums")
+
+
+def kgs_close_sums(ctx, sums_dev):
+    """Closure from the summed per-cell sums at the device pointer sums_dev; returns (rc, residual).
+    KGS_EDIVERGED is returned, other errors raise."""
+    res = ctypes.c_double(0.0)
+    rc = load().kgs_close_sums(ctx.handle, ctypes.c_void_p(sums_dev), ctypes.byref(res))
+    _check(rc, "kgs_close_sums", allow=(KGS_EDIVERGED,))
+    return rc, res.value
+
+
 def kgs_destroy(ctx):
     if ctx.handle:
         load().kgs_destroy(ctx.handle)
@@ -312,7 +333,8 @@ def kgs_iterate_noalloc(prob, macros_in, rho_w_in, macros_out, rho_w_out, M0=0.0
 
 class KgsProblem(ctypes.Structure):
     _fields_ = [("grid", KgsGrid), ("solid", ctypes.POINTER(ctypes.c_uint8)), ("vgrid", KgsVgrid),
-                ("gas", KgsGas), ("bc", KgsBc), ("wall_norm", ctypes.c_int), ("mass_rescale", ctypes.c_int)]
+                ("gas", KgsGas), ("bc", KgsBc), ("wall_norm", ctypes.c_int), ("mass_rescale", ctypes.c_int),
+                ("q_lagged", ctypes.c_int)]
 
 
 SIGNATURES.update({
@@ -327,13 +349,17 @@ SIGNATURES.update({
     "kgs_batch_profile": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_longlong)]),
     "kgs_batch_fault": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int]),
+    "kgs_batch_solve": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(KgsProblem),
+                                       ctypes.POINTER(KgsOpts), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), _dp]),
     "kgs_batch_destroy": (None, [ctypes.c_void_p]),
 })
 
 
 def _problem(prob, keep):
     g, v, gas, bc, solid_p = _problem_structs(prob, keep)
-    return KgsProblem(g, solid_p, v, gas, bc, int(prob.wall_mode), int(prob.mass_rescale))
+    return KgsProblem(g, solid_p, v, gas, bc, int(prob.wall_mode), int(prob.mass_rescale),
+                      int(getattr(prob, "q_lagged", 0)))
 
 
 def kgs_autotune(prob, precision=KGS_MIXED):
@@ -376,6 +402,23 @@ def kgs_batch_iterate(b, n_iters=1):
     rc = load().kgs_batch_iterate(b.handle, int(n_iters), done, res)
     _check(rc, "kgs_batch_iterate", allow=(KGS_NOTCONVERGED, KGS_EDIVERGED, KGS_ETIMEOUT))
     return rc, list(done), list(res)
+
+
+def kgs_batch_solve(probs, tol=1e-6, max_iters=1000, v_per_cta=0, block_z=0, stream=None):
+    """kgs_batch_solve: mixed then FP64 per instance.  Returns (rc, batch, iterations in the mixed phase,
+    iterations in the FP64 phase, final residuals); the batch holds the FP64 results.  KGS_NOTCONVERGED
+    is returned, other errors raise."""
+    keep = []
+    n = len(probs)
+    arr = (KgsProblem * n)(*[_problem(p, keep) for p in probs])
+    opts = KgsOpts(KGS_MIXED, 0, 0, max_iters, tol, v_per_cta, block_z, ctypes.c_void_p(stream) if stream else None)
+    h = ctypes.c_void_p()
+    im = (ctypes.c_int * n)()
+    idd = (ctypes.c_int * n)()
+    res = (ctypes.c_double * n)()
+    rc = load().kgs_batch_solve(ctypes.byref(h), n, arr, ctypes.byref(opts), im, idd, res)
+    _check(rc, "kgs_batch_solve", allow=(KGS_NOTCONVERGED,))
+    return rc, Batch(h, probs), list(im), list(idd), list(res)
 
 
 def kgs_batch_moments(b, i):

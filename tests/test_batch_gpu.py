@@ -97,3 +97,21 @@ def test_autotune_picks_a_valid_cached_shape(kgs):
     b = kgs.kgs_batch_setup([p, inputs.cavity(6, 6)], precision=1)
     info = kgs.kgs_batch_info(b, 0)
     assert (info["v_per_cta"], info["block_z"]) == (vpc, bz)
+
+
+def test_batch_solve_equals_kgs_solve_per_instance(kgs):
+    """kgs_batch_solve applies kgs_solve's switch rule to every instance of a
+    batch: with the same sweep shapes (256 velocities per thread block in the
+    mixed phase, 128 in FP64, blocks 32 cells deep) each instance follows the
+    same mixed iterations, switches at the same iteration and ends on the same
+    FP64 state, bit for bit."""
+    probs = inputs.batch_cavities(n=4, seed=11, cells=(6, 12), vels=(8, 12))
+    rc, b, nm, nd, res = kgs.kgs_batch_solve(probs, tol=1e-6, max_iters=2000, v_per_cta=256, block_z=32)
+    assert rc == kgs.KGS_OK
+    assert all(r < 1e-6 for r in res)
+    for i, p in enumerate(probs):
+        rc1, m1, nm1, nd1, r1 = kgs.kgs_solve(p, tol=1e-6, max_iters=2000)
+        assert rc1 == kgs.KGS_OK
+        assert (nm[i], nd[i]) == (nm1, nd1), i
+        assert res[i] == r1
+        assert np.array_equal(kgs.kgs_batch_moments(b, i), m1), i

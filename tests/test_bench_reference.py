@@ -1,6 +1,6 @@
 """The benchmark's reference arm (the FP64 oracle timed on a bounded sample
-of the workload on one host core) prints one JSON line with the contract's
-keys; it needs no GPU."""
+of the workload on the host's cores) prints one JSON line with the
+contract's keys; it needs no GPU."""
 import json
 import os
 import subprocess
@@ -23,5 +23,5 @@ def test_reference_arm_prints_one_json_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and 1 <= d["cpu_baseline"]["cores"] <= (os.cpu_count() or 1)
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0

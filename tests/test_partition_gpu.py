@@ -1,0 +1,85 @@
+"""Velocity-space partition and the lagged heat flux through the C ABI.
+
+The paper's CPU twin splits the velocities of an outer iteration over MPI
+ranks and sums their moments with MPI_Allreduce (Section 5): velocities are
+independent within an iteration because Eq. (6) lags f^S, tau and rho_w.
+Here two contexts of the same problem each sweep half of the velocity planes
+(kgs_opts.vz_begin / vz_end), one after the other on one GPU; their per-cell
+sums are added on the host in a fixed order (the all-reduce), and both close
+the iteration from the total.  The fields must equal those of the context
+that sweeps every velocity.
+
+The heat flux about the lagged velocity (Algorithm 3's one-pass moments,
+kgs_opts.q_lagged) is compared with the oracle's option of the same name.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1810_00348_gb300 import inputs
+from tests.parity import assert_fields_close, assert_rho_w_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kgs():
+    from paper_1810_00348_gb300 import kgs as k
+    k.load()
+    return k
+
+
+@pytest.mark.parametrize("precision,tol,res_tol", [(0, 1e-12, 1e-11), (1, 1e-9, 1e-7)])
+def test_two_velocity_ranges_equal_the_whole(kgs, precision, tol, res_tol):
+    import torch
+
+    p = inputs.cavity([19, 13, 17], [10, 9, 12], L_v=4.0, lid=0.2, Kn=0.3)
+    mac = inputs.random_macros(p, 901)
+    whole = kgs.kgs_setup(p, precision=precision)
+    kgs.kgs_set_initial(whole, mac)
+    nvz = len(p.xi_z)
+    parts = [kgs.kgs_setup(p, precision=precision, vz=(0, 5)), kgs.kgs_setup(p, precision=precision, vz=(5, nvz))]
+    for c in parts:
+        kgs.kgs_set_initial(c, mac)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sums = [torch.empty(19 * p.ncell, dtype=torch.float64, device=dev) for _ in parts]
+    total = torch.empty_like(sums[0])
+    for _ in range(3):
+        for c, s in zip(parts, sums):
+            kgs.kgs_sweep_sums(c, s.data_ptr())
+        host = [s.cpu().numpy() for s in sums]
+        total.copy_(torch.from_numpy(host[0] + host[1]))  # fixed order: part 0 + part 1
+        res = [kgs.kgs_close_sums(c, total.data_ptr()) for c in parts]
+        rc, _, r_whole = kgs.kgs_iterate(whole, 1)
+        assert rc == kgs.KGS_OK
+        assert res[0] == res[1]
+        # the parts add their sums in another order than the whole: equal to rounding
+        assert abs(res[0][1] - r_whole) <= res_tol * r_whole
+    ref = kgs.kgs_moments(whole)
+    for c in parts:
+        assert np.array_equal(kgs.kgs_moments(c), kgs.kgs_moments(parts[0]))
+        assert_fields_close(kgs.kgs_moments(c), ref, tol, what="velocity partition, precision %d" % precision)
+        assert_rho_w_close(kgs.kgs_rho_w(c), kgs.kgs_rho_w(whole), tol)
+
+
+def test_partition_rejects_bad_ranges(kgs):
+    p = inputs.cavity(6, 8)
+    for vz in ((3, 3), (-1, 4), (4, 9), (5, 2)):
+        with pytest.raises(kgs.KgsError) as e:
+            kgs.kgs_setup(p, vz=vz)
+        assert e.value.code == kgs.KGS_EINVAL
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-5)])
+def test_lagged_heat_flux_against_oracle(kgs, precision, tol):
+    p = inputs.cavity([14, 11, 12], [9, 8, 10], L_v=3.5, lid=0.2, Kn=0.4)
+    p.q_lagged = 1
+    mac = inputs.random_macros(p, 905)
+    o = Oracle(p, mac)
+    o.iterate(2)
+    c = kgs.kgs_setup(p, precision=precision)
+    kgs.kgs_set_initial(c, mac)
+    rc, done, _ = kgs.kgs_iterate(c, 2)
+    assert rc == kgs.KGS_OK and done == 2
+    assert_fields_close(kgs.kgs_moments(c), o.macros(), tol, what="lagged q, precision %d" % precision)
+    assert_rho_w_close(kgs.kgs_rho_w(c), o.rho_w(), tol)
