@@ -258,20 +258,29 @@ __global__ void __launch_bounds__(256) acc_sums_kernel(const AccSumArgs a)
 {
     const size_t ncell = a.ncell;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncell * NACC) return;
-    const size_t c = i / NACC;
-    const int q = (int)(i % NACC);
-    if (q >= NSUM) return;
+    if (i >= ncell * NSUM) return;
+    const size_t c = i / NSUM;
+    const int q = (int)(i % NSUM);
+    const int side = q - SUM_F0;
+    // the accumulator slot of sum slot q (compact layout: the flux of an axis
+    // belongs to the side that has a wall, zero on the other side)
+    int slot = q;
+    bool zero = false;
+    if (side >= 0 && a.acc_slots == ACC_COMPACT) {
+        slot = SUM_F0 + side / 2;
+        zero = a.wall_kind[(size_t)side * ncell + c] < 0;
+    }
     double v = 0.0;
-    if (!(a.solid && a.solid[c])) {
+    if (!(a.solid && a.solid[c]) && !zero) {
+        const size_t at = c * a.acc_slots + slot, ks = ncell * a.acc_slots;
         if (sizeof(Real) == 8) {
-            const double *p = static_cast<const double *>(a.acc) + i;
-            for (int k = 0; k < a.nacc; k++) v += p[(size_t)k * ncell * NACC];
+            const double *p = static_cast<const double *>(a.acc) + at;
+            for (int k = 0; k < a.nacc; k++) v += p[(size_t)k * ks];
         } else {
-            const float2 *p = static_cast<const float2 *>(a.acc) + i;
+            const float2 *p = static_cast<const float2 *>(a.acc) + at;
             FFSum t;
             for (int k = 0; k < a.nacc; k++) {
-                const float2 e = p[(size_t)k * ncell * NACC];
+                const float2 e = p[(size_t)k * ks];
                 t.add(e.x, 0.f);
                 t.add(e.y, 0.f);
             }
@@ -281,8 +290,8 @@ __global__ void __launch_bounds__(256) acc_sums_kernel(const AccSumArgs a)
                 double U[3];
                 centre32(a.coef, c, U);
                 v += ref_slot(a.ref, q, U);
-            } else if (a.wall_kind[(size_t)(q - SUM_F0) * ncell + c] >= 0) {
-                v += a.ref.flux[q - SUM_F0];
+            } else if (a.wall_kind[(size_t)side * ncell + c] >= 0) {
+                v += a.ref.flux[side];
             }
         }
     }
@@ -567,7 +576,7 @@ cudaError_t launch_part_sums(const PartSumArgs &a, cudaStream_t s)
 
 cudaError_t launch_acc_sums(const AccSumArgs &a, cudaStream_t s)
 {
-    const unsigned nb = nblk((size_t)a.ncell * NACC, 256);
+    const unsigned nb = nblk((size_t)a.ncell * NSUM, 256);
     if (a.precision == 0)
         acc_sums_kernel<double><<<nb, 256, 0, s>>>(a);
     else

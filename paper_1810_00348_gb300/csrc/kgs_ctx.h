@@ -26,7 +26,7 @@ struct kgs_ctx {
     void *coef = nullptr, *vel = nullptr, *velm = nullptr, *mtab = nullptr, *FX = nullptr, *FY = nullptr,
          *FZ = nullptr;
     void *part = nullptr;   // staged sweep only: per-(group, cell) partials
-    void *acc = nullptr;    // persistent sweep: ordered accumulators [nacc][ncell][NACC]
+    void *acc = nullptr;    // persistent sweep: ordered accumulators [nacc][ncell][acc_slots]
     int use_acc = 0;        // the sweep runs persistent and adds into acc
     double *sums = nullptr; // [NSUM][ncell] per-cell sums of the iteration (FP64)
     double *vel64 = nullptr, *axis64 = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;

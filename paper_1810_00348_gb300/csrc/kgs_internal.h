@@ -54,9 +54,15 @@ enum {
 // the wall on each domain side s (-x, +x, -y, +y, -z, +z) at slot SUM_F0 + s.
 constexpr int SUM_F0 = 13;
 constexpr int NSUM = 19;
-// Ordered accumulators of the persistent sweep: [nacc][ncell][NACC] (FP64, or
-// float-float pairs (hi, lo) for the FP32 path); slots as the sums above.
-constexpr int NACC = 20;
+// Ordered accumulators of the persistent sweep: [nacc][ncell][acc_slots] (FP64,
+// or float-float pairs (hi, lo) for the FP32 path).  ACC_COMPACT slots: the
+// 13 sums, then one incoming flux per axis -- the flux onto the only wall a
+// cell has along that axis -- the layout of an item's partials, so that an
+// item adds its record element-wise.  ACC_SPLIT slots: the 13 sums, then one
+// flux per side (slot SUM_F0 + side), for problems where some cell has walls
+// on both sides along an axis.
+constexpr int ACC_COMPACT = 16;
+constexpr int ACC_SPLIT = 20;
 constexpr int NACC_MAX = 8;  // accumulators per instance, at most
 
 // Reference Maxwellian of the FP32 sweep, which carries g = f - M_ref rather
@@ -103,8 +109,9 @@ struct SweepArgs {
     void *FX, *FY, *FZ;           // face planes: [nz*ny][Nv], [nz*nx][Nv], [ny*nx][Nv]
     void *part;                   // staged sweep: [n_vg][ncell][NPART], double (FP64 path) or
                                   // float2 (s, c) with value s - c (FP32 path, Kahan pair)
-    void *acc;                    // persistent sweep: [nacc][ncell][NACC] ordered accumulators
+    void *acc;                    // persistent sweep: [nacc][ncell][acc_slots] ordered accumulators
     int nacc;                     // accumulators: velocity group g of an octant adds into g % nacc
+    int acc_slots;                // ACC_COMPACT or ACC_SPLIT
     int *tok;                     // persistent sweep: [nacc][nbz][nby][nbx] chain tokens
     unsigned long long ncell;
     int line16;                   // every octant has x-lines of 16 nodes (specialised moment loop)
@@ -221,6 +228,7 @@ struct AccSumArgs {
     int precision;
     const void *acc;
     int nacc;
+    int acc_slots;
     unsigned long long ncell;
     const uint8_t *solid;         // [ncell] or NULL
     double *sums;                 // [NSUM][ncell]

@@ -168,6 +168,7 @@ SweepArgs kgs::ctx_sweep_args(const kgs_ctx *c)
     a.part = c->part;
     a.acc = c->acc;
     a.nacc = t.nacc;
+    a.acc_slots = t.acc_slots;
     a.tok = c->p_tok;
     a.ncell = t.ncell;
     a.line16 = 1;
@@ -268,7 +269,7 @@ void kgs::chain_positions(const std::vector<int4> &items, const std::vector<cons
 int kgs::ctx_alloc_acc(kgs_ctx *c)
 {
     const HostTables &t = c->t;
-    const size_t bytes = (size_t)t.nacc * t.ncell * NACC * 8;
+    const size_t bytes = (size_t)t.nacc * t.ncell * t.acc_slots * 8;
     int rc = dalloc(c, &c->acc, bytes);
     if (rc) return rc;
     // every slot read by the sums is stored by the first item of its chain in
@@ -319,6 +320,7 @@ int kgs::ctx_launch_sums(kgs_ctx *c)
         aa.precision = t.precision;
         aa.acc = c->acc;
         aa.nacc = t.nacc;
+        aa.acc_slots = t.acc_slots;
         aa.ncell = t.ncell;
         aa.solid = c->solid;
         aa.sums = c->sums;

@@ -72,7 +72,7 @@ __device__ __forceinline__ float rcp_approx(float x)
 // log2(e) factor already folded into the coefficient C_NEXP.
 __device__ __forceinline__ double eq_exp(double x) { return exp(x); }
 __device__ __forceinline__ float eq_exp(float x) { return ex2_approx(x); }
-// FP64: the reciprocal of the denominator from the hardware approximation
+// FP64 implicit update: the reciprocal of the denominator from the hardware approximation
 // refined by two Newton-Raphson steps r <- r + r (1 - den r) (quadratic
 // convergence, about 1 ulp), then one product; den = 1/tau + sum a_d > 0.
 __device__ __forceinline__ double implicit_div(double num, double den)
@@ -83,7 +83,6 @@ __device__ __forceinline__ double implicit_div(double num, double den)
     r = fma(r, fma(-den, r, 1.0), r);
     return num * r;
 }
-__device__ __forceinline__ float implicit_div(float num, float den) { return num * rcp_approx(den); }
 
 __host__ __device__ constexpr size_t align16(size_t n) { return (n + 15) & ~size_t(15); }
 
@@ -466,6 +465,87 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         if (lk + 1 < ez) prefetch(lk + 1);
 
         // ---- sweep of the slice: Eq. (2) fused into Eq. (7), by anti-diagonals ----
+        // Eq. (2) fused into Eq. (7) for one cell of the slice (coefficients
+        // c0..c3) and thread velocity m, from its three upwind values.
+        auto cell_update = [&](const Quad<Real> &c0, const Quad<Real> &c1, const Quad<Real> &c2v,
+                               const Quad<Real> &c3, int m, Real fx, Real fy, Real fz) -> Real {
+            const Real m2ux = c0.x, m2uy = c0.y, m2uz = c0.z, kappa = c0.w;
+            const Real nexp = c1.x, rt1 = c1.y, rtau = c1.z;
+            const Real qx = c2v.x, qy = c2v.y, qz = c2v.z, rdx = c2v.w;
+            const Real rdy = c3.x, rdz = c3.y, shk0 = c3.z, muq = c3.w;
+            // |c|^2 - |U|^2 = |xi|^2 - 2 U.xi and c.q' = xi.q' - U.q'
+            const Real s = fma(xi[m][0], m2ux, fma(xi[m][1], m2uy, fma(xi[m][2], m2uz, xsq[m])));
+            const Real cq = fma(xi[m][0], qx, fma(xi[m][1], qy, fma(xi[m][2], qz, muq)));
+            const Real shak = fma(cq, fma(s, rt1, shk0), Real(1));
+            Real src;
+            if constexpr (sizeof(Real) == 4)  // kappa enters as log2(kappa) in the exponent
+                src = eq_exp(fma(s, nexp, kappa)) * shak;
+            else
+                src = kappa * eq_exp(s * nexp) * shak;
+            Real ax, ay, az, den;
+            if constexpr (UNIF) {
+                ax = adx[m][0];
+                ay = adx[m][1];
+                az = adx[m][2];
+                den = rtau + asum[m];
+            } else {
+                ax = axi[m][0] * rdx;
+                ay = axi[m][1] * rdy;
+                az = axi[m][2] * rdz;
+                den = rtau + ax + ay + az;
+            }
+            if constexpr (sizeof(Real) == 4) {
+                // The same solution of Eq. (7) written about the upwind x value:
+                //   f = f_x + (src - f_x/tau + a_y (f_y - f_x) + a_z (f_z - f_x)) / den.
+                // On a smooth field the increment is small, so the one rounding
+                // that matters is the final addition, which is unbiased.  The
+                // plain form num * (1/den) scales f by the same rounding error of
+                // 1/den in every cell of a velocity's characteristic, and that
+                // error adds up along the sweep.
+                (void)ax;
+                Real t = fma(-rtau, fx + mref[m], src);
+                t = fma(ay, fy - fx, t);
+                t = fma(az, fz - fx, t);
+                return fma(t, rcp_approx(den), fx);
+            } else {
+                return implicit_div(src + ax * fx + ay * fy + az * fz, den);
+            }
+        };
+        if (ex == BX && ey == BY && !any_solid) {
+            // Full block without solid cells: the 15 diagonals unrolled.  The
+            // upwind x and y values of a cell were computed on the previous
+            // diagonal by this thread and stay in registers (prev[row]); only
+            // the z value (the cell itself in slice k-1) and the halo row and
+            // column come from shared memory.  Every index is a compile-time
+            // constant, so the cells of a diagonal form straight-line code whose
+            // update chains the compiler can interleave, and a diagonal waits
+            // only for register results of the one before.
+            Real prev[BY][TV];
+#pragma unroll
+            for (int d = 0; d < BX + BY - 1; d++) {
+#pragma unroll
+                for (int k = 0; k < BY; k++) {
+                    const int lj = (d < BY - 1 ? d : BY - 1) - k;
+                    const int li = d - lj;
+                    if (lj >= 0 && li < BX) {
+                        const Real *c = cs + (lj * BX + li) * NCOEF;
+                        const Quad<Real> c0 = load_quad(c), c1 = load_quad(c + 4), c2v = load_quad(c + 8),
+                                         c3 = load_quad(c + 12);
+                        const int sidx = SL(li, lj);
+#pragma unroll
+                        for (int m = 0; m < TV; m++) {
+                            const int vl = t + m * NT;
+                            const Real fz = slice[sidx + vl];
+                            const Real fx = li == 0 ? slice[sidx - CS + vl] : prev[lj][m];
+                            const Real fy = lj == 0 ? slice[sidx - (BX + 1) * CS + vl] : prev[lj > 0 ? lj - 1 : 0][m];
+                            const Real f = cell_update(c0, c1, c2v, c3, m, fx, fy, fz);
+                            prev[lj][m] = f;
+                            if (ok[m]) slice[sidx + vl] = f;
+                        }
+                    }
+                }
+            }
+        } else {
         // The upwind values of cell (i, j) are read from the in-place slice:
         // (i-1, j) and (i, j-1) were updated on the previous diagonal, (i, j)
         // itself still holds slice k-1.  The cells of one diagonal are
@@ -480,11 +560,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                     const Real *c = cs + (lj * BX + li) * NCOEF;
                     const Quad<Real> c0 = load_quad(c), c1 = load_quad(c + 4), c2v = load_quad(c + 8),
                                      c3 = load_quad(c + 12);
-                    const Real m2ux = c0.x, m2uy = c0.y, m2uz = c0.z, kappa = c0.w;
-                    const Real nexp = c1.x, rt1 = c1.y, rtau = c1.z;
                     const int flags = flag_bits(c1.w);
-                    const Real qx = c2v.x, qy = c2v.y, qz = c2v.z, rdx = c2v.w;
-                    const Real rdy = c3.x, rdz = c3.y, shk0 = c3.z, muq = c3.w;
                     if (!(flags & F_SOLID)) {
                         bool sol_x = false, sol_y = false, sol_z = false;
                         Real rwx = 0, rwy = 0, rwz = 0;
@@ -509,49 +585,13 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                                 if (sol_y) fy = ghost(rwy, msol[m], m);
                                 if (sol_z) fz = ghost(rwz, msol[m], m);
                             }
-                            // |c|^2 - |U|^2 = |xi|^2 - 2 U.xi and c.q' = xi.q' - U.q'
-                            const Real s = fma(xi[m][0], m2ux, fma(xi[m][1], m2uy, fma(xi[m][2], m2uz, xsq[m])));
-                            const Real cq = fma(xi[m][0], qx, fma(xi[m][1], qy, fma(xi[m][2], qz, muq)));
-                            const Real shak = fma(cq, fma(s, rt1, shk0), Real(1));
-                            Real src;
-                            if constexpr (sizeof(Real) == 4)  // kappa enters as log2(kappa) in the exponent
-                                src = eq_exp(fma(s, nexp, kappa)) * shak;
-                            else
-                                src = kappa * eq_exp(s * nexp) * shak;
-                            Real ax, ay, az, den;
-                            if constexpr (UNIF) {
-                                ax = adx[m][0];
-                                ay = adx[m][1];
-                                az = adx[m][2];
-                                den = rtau + asum[m];
-                            } else {
-                                ax = axi[m][0] * rdx;
-                                ay = axi[m][1] * rdy;
-                                az = axi[m][2] * rdz;
-                                den = rtau + ax + ay + az;
-                            }
-                            Real f;
-                            if constexpr (sizeof(Real) == 4) {
-                                // The same solution of Eq. (7) written about the upwind x value:
-                                //   f = f_x + (src - f_x/tau + a_y (f_y - f_x) + a_z (f_z - f_x)) / den.
-                                // On a smooth field the increment is small, so the one rounding
-                                // that matters is the final addition, which is unbiased.  The
-                                // plain form num * (1/den) scales f by the same rounding error of
-                                // 1/den in every cell of a velocity's characteristic, and that
-                                // error adds up along the sweep.
-                                Real t = fma(-rtau, fx + mref[m], src);
-                                t = fma(ay, fy - fx, t);
-                                t = fma(az, fz - fx, t);
-                                f = fma(t, rcp_approx(den), fx);
-                                (void)ax;
-                            } else {
-                                f = implicit_div(src + ax * fx + ay * fy + az * fz, den);
-                            }
+                            const Real f = cell_update(c0, c1, c2v, c3, m, fx, fy, fz);
                             if (ok[m]) slice[sidx + vl] = f;
                         }
                     }
                 }
             }
+        }
         }
         // outflow of the slice through the block's downwind x and y faces, for
         // the neighbouring blocks (own velocities, read back from the slice)
@@ -864,42 +904,135 @@ __device__ bool wait_token(const int *p, int v, long long limit)
 // form a chain in the order they were claimed, and the item at place `pos`
 // adds after the one at pos - 1 (the first one stores).  The order is fixed
 // by the work list, so the sums are bit-reproducible, and no item waits for
-// one claimed after it.  The flux slots of the item (incoming flux onto the
-// wall ahead of its octant along x, y, z) go to the slots of those sides.
-// FP32 partials are Kahan pairs (s, c) with value s - c; the accumulator holds
-// a float-float pair (hi, lo) with value hi + lo, hi updated by a two-sum.
+// one claimed after it.  FP32 partials are Kahan pairs (s, c) with value
+// s - c; the accumulator holds a float-float pair (hi, lo) with value hi + lo,
+// hi updated by a two-sum.
+template <typename Real>
+struct Acc16;
+template <>
+struct Acc16<double> {
+    using V = double2;  // two slots
+    __device__ static V init(V s) { return s; }
+    __device__ static V add(V a, V s) { return make_double2(a.x + s.x, a.y + s.y); }
+};
+template <>
+struct Acc16<float> {
+    using V = float4;  // two slots: (s0, c0, s1, c1) / (hi0, lo0, hi1, lo1)
+    __device__ static V init(V s) { return make_float4(s.x, -s.y, s.z, -s.w); }
+    __device__ static float2 ff(float hi, float lo, float s, float c)
+    {
+        const float t = hi + s;
+        const float bp = t - hi;
+        const float err = (hi - (t - bp)) + (s - bp);
+        return make_float2(t, lo + (err - c));
+    }
+    __device__ static V add(V a, V s)
+    {
+        const float2 p = ff(a.x, a.y, s.x, s.y), q = ff(a.z, a.w, s.z, s.w);
+        return make_float4(p.x, p.y, q.x, q.y);
+    }
+};
+
+// Block geometry of an item for the chain: physical extents and origin.
+struct BlockSpan {
+    bool px, py, pz;
+    int x0, ex, y0, ey, z0, ez;
+    __device__ BlockSpan(const SweepArgs &a, int o, int bxr, int byr, int bzr)
+    {
+        px = (o & 1) != 0, py = (o & 2) != 0, pz = (o & 4) != 0;
+        const int bxi = px ? bxr : a.nbx - 1 - bxr;
+        const int byi = py ? byr : a.nby - 1 - byr;
+        const int bzi = pz ? bzr : a.nbz - 1 - bzr;
+        x0 = bxi * BX, ex = min(BX, a.nx - x0);
+        y0 = byi * BY, ey = min(BY, a.ny - y0);
+        z0 = bzi * a.bz, ez = min(a.bz, a.nz - z0);
+    }
+    // global cell of the block's local (march-order) cell cl of slice lk
+    __device__ size_t cell(const SweepArgs &a, int cl, int lk) const
+    {
+        const int li = cl % BX, lj = cl / BX;
+        const int x = px ? x0 + li : x0 + ex - 1 - li;
+        const int y = py ? y0 + lj : y0 + ey - 1 - lj;
+        const int z = pz ? z0 + lk : z0 + ez - 1 - lk;
+        return (size_t)x + (size_t)a.nx * ((size_t)y + (size_t)a.ny * z);
+    }
+    __device__ bool valid(int cl) const { return cl % BX < ex && cl / BX < ey; }
+};
+
+// Before the chain wait: pull the block's accumulator records into L2.
+template <typename Real>
+__device__ void chain_prefetch(const SweepArgs &a, const BlockSpan &b, int vg)
+{
+    const unsigned char *acc = static_cast<const unsigned char *>(a.acc) +
+                               (size_t)(vg % a.nacc) * a.ncell * a.acc_slots * 8;
+    const int rec = a.acc_slots * 8;
+    for (int r = threadIdx.x; r < b.ez * BY; r += NT) {  // one row of ex cells
+        const int lj = r % BY, lk = r / BY;
+        if (lj >= b.ey) continue;
+        const unsigned char *p = acc + b.cell(a, lj * BX, lk) * rec;
+        const unsigned char *q = acc + b.cell(a, lj * BX + b.ex - 1, lk) * rec;
+        const unsigned char *lo = p < q ? p : q;
+        for (int off = 0; off < b.ex * rec; off += 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(lo + off));
+    }
+}
+
 template <typename Real>
 __device__ void chain_add(const SweepArgs &a, int o, int bxr, int byr, int bzr, int vg, int pos,
                           const void *scratch)
 {
     using Out = typename PartOut<Real>::T;
-    const bool px = (o & 1) != 0, py = (o & 2) != 0, pz = (o & 4) != 0;
-    const int bxi = px ? bxr : a.nbx - 1 - bxr;
-    const int byi = py ? byr : a.nby - 1 - byr;
-    const int bzi = pz ? bzr : a.nbz - 1 - bzr;
-    const int x0 = bxi * BX, ex = min(BX, a.nx - x0);
-    const int y0 = byi * BY, ey = min(BY, a.ny - y0);
-    const int z0 = bzi * a.bz, ez = min(a.bz, a.nz - z0);
+    const BlockSpan b(a, o, bxr, byr, bzr);
     const size_t ncell = a.ncell;
+    if (a.acc_slots == ACC_COMPACT) {
+        // the item's record and the accumulator record share one layout: add
+        // them element-wise, 16 bytes (two slots) at a time, with CH vectors
+        // of every thread in flight
+        using A = Acc16<Real>;
+        using V = typename A::V;
+        constexpr int VPC = NPART * 8 / 16;  // vectors per cell record
+        constexpr int CH = 4;
+        const V *sc = static_cast<const V *>(scratch);
+        V *acc = reinterpret_cast<V *>(static_cast<Out *>(a.acc) + (size_t)(vg % a.nacc) * ncell * ACC_COMPACT);
+        const int n = b.ez * SLICE * VPC;
+        for (int base = threadIdx.x; base < n; base += NT * CH) {
+            V sv[CH], av[CH];
+            size_t at[CH];
+            bool live[CH];
+#pragma unroll
+            for (int u = 0; u < CH; u++) {
+                const int e = base + u * NT;
+                const int lc = e / VPC, cl = lc % SLICE;
+                live[u] = e < n && b.valid(cl);
+                at[u] = live[u] ? b.cell(a, cl, lc / SLICE) * VPC + e % VPC : 0;
+                if (live[u]) sv[u] = sc[e];  // written by this CTA: the same L1 path
+            }
+            if (pos > 0) {
+#pragma unroll
+                for (int u = 0; u < CH; u++)
+                    if (live[u]) av[u] = __ldcg(acc + at[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < CH; u++)
+                if (live[u]) acc[at[u]] = pos == 0 ? A::init(sv[u]) : A::add(av[u], sv[u]);
+        }
+        return;
+    }
+    // ACC_SPLIT: the item's flux slots go to the slots of the sides ahead of
+    // its octant; the first item of the chain stores zero on the other sides
     const Out *sc = static_cast<const Out *>(scratch);
-    Out *acc = static_cast<Out *>(a.acc) + (size_t)(vg % a.nacc) * ncell * NACC;
-    const int n = ez * SLICE * NPART;
+    Out *acc = static_cast<Out *>(a.acc) + (size_t)(vg % a.nacc) * ncell * ACC_SPLIT;
+    const int n = b.ez * SLICE * NPART;
 #pragma unroll 4
     for (int e = threadIdx.x; e < n; e += NT) {
         const int q = e % NPART, cl = (e / NPART) % SLICE, lk = e / (NPART * SLICE);
-        const int li = cl % BX, lj = cl / BX;
-        if (li >= ex || lj >= ey) continue;
-        const int x = px ? x0 + li : x0 + ex - 1 - li;
-        const int y = py ? y0 + lj : y0 + ey - 1 - lj;
-        const int z = pz ? z0 + lk : z0 + ez - 1 - lk;
-        const size_t cell = (size_t)x + (size_t)a.nx * ((size_t)y + (size_t)a.ny * z);
+        if (!b.valid(cl)) continue;
+        const size_t cell = b.cell(a, cl, lk);
         const int slot = q < P_FX ? q : SUM_F0 + 2 * (q - P_FX) + ((o >> (q - P_FX)) & 1);
         const Out v = sc[e];  // written by this CTA: the same L1 path
-        Out *dst = acc + cell * NACC + slot;
+        Out *dst = acc + cell * ACC_SPLIT + slot;
         if (pos == 0 && q >= P_FX) {
-            // the first item of the chain stores every slot: the flux onto the
-            // wall behind its octant is zero
-            Out *other = acc + cell * NACC + (SUM_F0 + 2 * (q - P_FX) + 1 - ((o >> (q - P_FX)) & 1));
+            Out *other = acc + cell * ACC_SPLIT + (SUM_F0 + 2 * (q - P_FX) + 1 - ((o >> (q - P_FX)) & 1));
             if constexpr (sizeof(Real) == 8)
                 *other = 0.0;
             else
@@ -975,6 +1108,7 @@ __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSwee
         const int byi = (o & 2) ? byr : sa.nby - 1 - byr;
         const int bzi = (o & 4) ? bzr : sa.nbz - 1 - bzr;
         int *tk = sa.tok + (((size_t)(vg % sa.nacc) * sa.nbz + bzi) * sa.nby + byi) * sa.nbx + bxi;
+        if (pos > 0) chain_prefetch<Real>(sa, BlockSpan(sa, o, bxr, byr, bzr), vg);
         if (threadIdx.x == 0) {
             bool ok = pos == 0 || wait_token(tk, pos, b.spin_limit);
             if (!ok) atomicExch(b.error, 1);

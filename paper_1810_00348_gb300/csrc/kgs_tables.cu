@@ -271,6 +271,13 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
                 }
             }
 
+    // accumulator layout: one flux slot per axis unless some cell has walls
+    // on both of its sides along an axis
+    t.acc_slots = ACC_COMPACT;
+    for (size_t c = 0; c < n && t.acc_slots == ACC_COMPACT; c++)
+        for (int d = 0; d < 3; d++)
+            if (t.wall_kind[(2 * d) * n + c] >= 0 && t.wall_kind[(2 * d + 1) * n + c] >= 0) t.acc_slots = ACC_SPLIT;
+
     // ---- wavefront stages over blocks ----
     t.nbx = (nx + BX - 1) / BX;
     t.nby = (ny + BY - 1) / BY;

@@ -28,6 +28,7 @@ struct HostTables {
     int oct_vstart[8] = {0}, oct_vcount[8] = {0}, oct_vgbase[8] = {0}, oct_nx[8] = {0};
     int n_vg = 0, max_vg = 0, nxo_max = 1;
     int nacc = 1;                            // ordered accumulators of the persistent sweep
+    int acc_slots = ACC_COMPACT;             // ACC_SPLIT if a cell has walls on both sides along an axis
     std::vector<int> vg_oct;                 // octant of each velocity group
     std::vector<double> vel64;               // [Nv][4] xi_x, xi_y, xi_z, w
     std::vector<double> axis64;              // 1D nodes and weights: xi_x, xi_y, xi_z, w_x, w_y, w_z

@@ -161,6 +161,42 @@ def cube(nx: int = 96, ny: int = 64, nz: int = 64, n_vel: int = 48, L_v: float =
                    name="cube %dx%dx%d x %d^3 Ma=%g Kn=%g" % (nx, ny, nz, n_vel, mach, Kn))
 
 
+def geometric_widths(n_inner: int, n_out_lo: int, r_lo: float, n_out_hi: int, r_hi: float, side: float = 1.0):
+    """Cell widths along one axis of a body of length `side`: n_inner equal
+    cells across the body, then n_out_lo cells towards the low end and
+    n_out_hi towards the high end whose widths grow cell by cell by the ratios
+    r_lo and r_hi, starting from the body's cell width.  Returns the widths
+    (low end first) and the index of the first body cell."""
+    h0 = side / n_inner
+    lo = [h0 * r_lo ** k for k in range(n_out_lo, 0, -1)]
+    hi = [h0 * r_hi ** k for k in range(1, n_out_hi + 1)]
+    return np.array(lo + [h0] * n_inner + hi), n_out_lo
+
+
+def cube_paper_mesh(n_inner: int = 31, n_lat: int = 75, n_front: int = 75, n_rear: int = 85, n_vel: int = 48,
+                    L_v: float = 4.0, Kn: float = 1.0, mach: float = 2.0, gamma: float = 5.0 / 3.0) -> Problem:
+    """Supersonic flow past a cube on the stretched mesh of Section 4.2:
+    181 x 181 x 191 cells (with the defaults) whose widths grow cell by cell
+    by 1.02 in front of and beside the unit cube and by 1.03 behind it, flow
+    along x; 48^3 uniform velocities on [-4, 4]^3; Kn 1, Ma 2, free stream on
+    every side, cube surface at the free-stream temperature.  Reading: the
+    paper gives the cell counts and ratios but its domain figure is missing;
+    n_inner cells span the cube, and the extents follow from the counts."""
+    wx, ix0 = geometric_widths(n_inner, n_front, 1.02, n_rear, 1.03)
+    wy, iy0 = geometric_widths(n_inner, n_lat, 1.02, n_lat, 1.02)
+    wz, iz0 = geometric_widths(n_inner, n_lat, 1.02, n_lat, 1.02)
+    nx, ny, nz = len(wx), len(wy), len(wz)
+    solid = np.zeros((nz, ny, nx), dtype=np.uint8)
+    solid[iz0:iz0 + n_inner, iy0:iy0 + n_inner, ix0:ix0 + n_inner] = 1
+    ax, aw = uniform_axis(n_vel, L_v)
+    u_inf = mach * math.sqrt(gamma / 2.0)
+    return Problem(nx=nx, ny=ny, nz=nz, dx=wx, dy=wy, dz=wz,
+                   xi_x=ax.copy(), xi_y=ax.copy(), xi_z=ax.copy(), w_x=aw.copy(), w_y=aw.copy(), w_z=aw.copy(),
+                   solid=solid, Kn=Kn, face_type=[FACE_INFLOW] * 6,
+                   rho_in=1.0, U_in=[u_inf, 0.0, 0.0], T_in=1.0, T_solid=1.0, mass_rescale=0,
+                   name="cube (stretched mesh) %dx%dx%d x %d^3 Ma=%g Kn=%g" % (nx, ny, nz, n_vel, mach, Kn))
+
+
 # --------------------------------------------------------------------------
 # seeded randomness
 

@@ -52,3 +52,26 @@ def test_velocity_axes():
     assert np.allclose(x, -x[::-1]) and math.isclose(x[-1], 8.0)
     d = np.diff(x)
     assert d[len(d) // 2] < d[0] / 5 and np.all(w > 0) and math.isclose(w.sum(), 16.0)
+
+
+def test_cube_on_the_papers_stretched_mesh():
+    """Section 4.2's mesh: 181 x 181 x 191 cells whose widths grow cell by
+    cell by 1.02 in front of and beside the unit cube and by 1.03 behind it
+    (flow along x), the cube spanned by equal cells, 48^3 uniform velocities
+    on [-4, 4]^3, Kn 1, Ma 2."""
+    p = inputs.cube_paper_mesh()
+    assert (p.nx, p.ny, p.nz) == (191, 181, 181)
+    assert len(p.xi_x) == 48 and p.xi_x[0] == -4.0 and p.xi_x[-1] == 4.0
+    assert p.Kn == 1.0 and abs(p.U_in[0] - 2.0 * np.sqrt(5.0 / 6.0)) < 1e-15
+    zs, ys, xs = np.nonzero(p.solid)
+    n = 31
+    assert p.solid.sum() == n ** 3
+    for w, lo in ((p.dx, xs.min()), (p.dy, ys.min()), (p.dz, zs.min())):
+        assert np.allclose(w[lo:lo + n], 1.0 / n)          # equal cells across the cube
+        assert abs(np.sum(w[lo:lo + n]) - 1.0) < 1e-12      # unit side
+    ratio = lambda w: w[1:] / w[:-1]
+    x0 = xs.min()
+    assert np.allclose(ratio(p.dx[:x0 + 1]), 1.0 / 1.02)     # front: growing away from the cube
+    assert np.allclose(ratio(p.dx[x0 + n - 1:]), 1.03)       # rear
+    y0 = ys.min()
+    assert np.allclose(ratio(p.dy[:y0 + 1]), 1.0 / 1.02) and np.allclose(ratio(p.dy[y0 + n - 1:]), 1.02)

@@ -29,7 +29,10 @@ def kgs():
     return k
 
 
-@pytest.mark.parametrize("precision,tol,res_tol", [(0, 1e-12, 1e-11), (1, 1e-9, 1e-7)])
+# FP32: the parts group the velocities of an x-line into thread blocks and
+# halves differently from the whole, so their FP32 line sums round
+# differently; they agree to FP32 accuracy, not to the last bit.
+@pytest.mark.parametrize("precision,tol,res_tol", [(0, 1e-12, 1e-11), (1, 1e-5, 1e-5)])
 def test_two_velocity_ranges_equal_the_whole(kgs, precision, tol, res_tol):
     import torch
 
