@@ -40,9 +40,9 @@ N_CELL, N_VEL, KN, LID = 64, 32, 1.0, 0.16
 # 13 (with the division); 13 moment sums about U^n 34.
 FLOPS_PER_PP = 68
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch (ncu, 32^3
-# cells x 32^3 velocities, 256 velocities per CTA, blocks 8x8x32): 2.108e9 B
+# cells x 32^3 velocities, 256 velocities per CTA, blocks 8x8x32): 2.897e9 B
 # over 1.074e9 phase points
-TRAFFIC_BYTES_PER_PP = 2.109e9 / 1.074e9
+TRAFFIC_BYTES_PER_PP = 2.897e9 / 1.074e9
 TRAFFIC_SHAPE = (256, 32)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -585,6 +585,8 @@ def run_config5(args, kgs, inputs, torch):
     out["training"] = {"samples": len(samples), "cells": 16, "vels": 16, "steps": args.c5_steps,
                        "data_s": t_data, "train_s": time.perf_counter() - t0,
                        "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-20:]))}
+    if args.only_c5:
+        print(json.dumps({"training": out["training"]}), flush=True)
     cases = []
     for kn in [float(v) for v in args.c5_kn.split(",") if v]:
         p = inputs.cavity(args.c5_cells, args.c5_vels, Kn=kn, lid=LID)
@@ -616,6 +618,8 @@ def run_config5(args, kgs, inputs, torch):
         case["network_gain_over_upsampled_s"] = case["mixed_fp64_upsampled_coarse"]["s"] - \
             case["mixed_fp64_network"]["s"]
         cases.append(case)
+        if args.only_c5:
+            print(json.dumps({"case": case}), flush=True)  # each case as it completes
     out["cases"] = cases
     return out
 
@@ -638,6 +642,7 @@ def main():
     ap.add_argument("--surrogate-cells", type=int, default=16, help="cells per side of the gain cavities")
     ap.add_argument("--surrogate-train", type=int, default=48, help="training cavities")
     ap.add_argument("--c5-kn", default="0.5", help="Knudsen numbers of the 128^3 time-to-1e-6 study (empty: skip)")
+    ap.add_argument("--only-c5", action="store_true", help="run only the time-to-1e-6 study and print its JSON")
     ap.add_argument("--c5-cells", type=int, default=128)
     ap.add_argument("--c5-vels", type=int, default=32)
     ap.add_argument("--c5-train", type=int, default=512, help="training cavities of the study's network")
@@ -648,6 +653,13 @@ def main():
     ap.add_argument("--vels", type=int, default=N_VEL, help="velocities per side (profiling runs only)")
     args = ap.parse_args()
     world, rank, local = dist_env()
+    if args.only_c5:
+        import torch
+
+        from paper_1810_00348_gb300 import inputs, kgs
+        kgs.load()
+        print(json.dumps(run_config5(args, kgs, inputs, torch)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -28,13 +28,20 @@
 // mask of the backward pass.
 //
 // The weight gradient (wgrad_tc_kernel) is the per-tap GEMM dW[t][co][ci] =
-// sum over voxels v of dy[v][co] in[v + off(t)][ci] with the voxels as the
-// reduction dimension.  Both tensors store voxels outermost, so a CTA loads
-// 8 x 16-voxel tiles with plain loads, transposes 8 x 8 bf16 blocks in
-// registers and writes them K-major (16-byte rows of 8 voxels of one
-// channel); output channels fill the 128 accumulator lanes (rows past Cout
-// are ignored).  A CTA accumulates a chunk of tiles of one sample for all 27
-// taps and writes its partial; the caller sums the partials in a fixed order.
+// sum over voxels v of dy[v][co] in[v + off(t)][ci], with the output
+// channels in the 128 accumulator lanes (rows past Cout are ignored), the
+// input channels as N and the voxels as the reduction dimension.  Both
+// stored tensors keep the channels of a voxel contiguous, which for this GEMM
+// is the MN-major operand layout (a core matrix is 8 voxels along K by 8
+// channels in 16 bytes; instruction-descriptor bits 15 and 16), so tiles move
+// with 16-byte cp.async and need no transpose.  A CTA takes the three taps
+// that share (kz, ky): three accumulators in tensor memory, and per 8 x 16
+// voxel tile one staged dy tile plus one 16 x 10 voxel block of input plane
+// z + kz - 1 whose x windows at offsets 0, 1, 2 are the three B operands.
+// Three tile buffers rotate (the copies of tile i + 2 in flight while the
+// MMAs of tile i run), each released by its commit barrier.  A CTA covers a
+// chunk of tiles of one sample and writes its partial; the caller sums the
+// partials in a fixed order.
 //
 // Every wait on a barrier is bounded; on expiry the CTA records the error,
 // waits (bounded) for its own MMAs, frees its tensor memory and returns.

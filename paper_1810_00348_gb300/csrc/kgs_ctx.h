@@ -31,7 +31,7 @@ struct kgs_ctx {
     double *sums = nullptr; // [NSUM][ncell] per-cell sums of the iteration (FP64)
     double *vel64 = nullptr, *axis64 = nullptr, *rdx = nullptr, *rdy = nullptr, *rdz = nullptr;
     double *ddx = nullptr, *ddy = nullptr, *ddz = nullptr;
-    uint8_t *solid = nullptr, *side_flags = nullptr;
+    uint8_t *solid = nullptr, *side_flags = nullptr, *blk_plain = nullptr;
     int8_t *wall_kind = nullptr;
     double *wall_norm = nullptr;
     int4 *work = nullptr;

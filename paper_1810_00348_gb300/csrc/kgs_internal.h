@@ -102,6 +102,7 @@ struct SweepArgs {
     int oct_nx[8];                // x nodes in each octant (length of its velocity x-lines)
     int nxo_max;                  // max over octants of oct_nx
     int any_solid;                // the problem has solid cells
+    const uint8_t *blk_plain;     // [nbz][nby][nbx]: 1 = no solid cell and no solid neighbour in the block (or NULL)
     const void *coef;             // Real[ncell][NCOEF]
     const double *rho_w;          // [6][ncell]
     const void *mtab;             // Real[MT_ROWS][Nv]: unit wall Maxwellians, free stream

@@ -4,11 +4,12 @@
 // macroscopic fields and wall densities (the whole solver state, Section 2.2:
 // the distribution is never stored), per-cell coefficients in the sweep
 // precision, octant-sorted velocity tables, the three face planes that carry
-// block faces between sweep stages, and the per-(velocity group, cell)
-// moment partials.  kgs_iterate launches, per outer iteration, the
-// coefficient kernel, one sweep launch per wavefront stage and four small
-// FP64 closure kernels, then reads back 16 bytes (residual and divergence
-// flag).
+// block faces between sweep stages, the ordered per-cell moment accumulators
+// with the work list, chain places and per-CTA scratch of the persistent
+// sweep, and the per-cell sums.  kgs_iterate launches, per outer iteration,
+// the coefficient kernel, one persistent sweep launch, the sums kernel and
+// four small FP64 closure kernels, then reads back 24 bytes (residual,
+// divergence flag and the wait-error word).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -158,6 +159,7 @@ SweepArgs kgs::ctx_sweep_args(const kgs_ctx *c)
     a.nxo_max = t.nxo_max;
     for (int o = 0; o < 8; o++) a.oct_nx[o] = t.oct_nx[o] > 0 ? t.oct_nx[o] : 1;
     a.any_solid = t.any_solid ? 1 : 0;
+    a.blk_plain = c->blk_plain;
     a.coef = c->coef;
     a.rho_w = c->rho_w;
     a.mtab = c->mtab;
@@ -504,7 +506,8 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
     } else {
         if ((rc = upload(c, reinterpret_cast<float **>(&c->velm), t.velm32))) return fail(rc);
     }
-    if (t.any_solid && (rc = upload(c, &c->solid, t.solid))) return fail(rc);
+    if (t.any_solid && ((rc = upload(c, &c->solid, t.solid)) || (rc = upload(c, &c->blk_plain, t.blk_plain))))
+        return fail(rc);
     if (cudaMemset(c->FX, 0, (size_t)t.nz * t.ny * t.Nv * rsz) != cudaSuccess ||
         cudaMemset(c->FY, 0, (size_t)t.nz * t.nx * t.Nv * rsz) != cudaSuccess ||
         cudaMemset(c->FZ, 0, (size_t)t.ny * t.nx * t.Nv * rsz) != cudaSuccess ||

@@ -39,12 +39,17 @@
 // xi_d - U_d are carried as float pairs (hi + lo, with first-order
 // corrections): their rounding would otherwise repeat identically on every
 // line and add up coherently in the heat flux.  The line folds go into
-// Kahan-compensated sums; the per-(group, cell) partial is written to global
-// memory (FP64, or an FP32 Kahan pair) and a fixed-order reduction closes the
-// iteration (no atomics).  Block faces between stages go through three face planes in
-// global memory indexed by the cell position on the face: a block reads the
-// plane entries written by its upwind neighbour in the previous stage before
-// overwriting them with its own outflow.
+// Kahan-compensated sums.  The per-(group, cell) partial (FP64, or an FP32
+// Kahan pair) goes to a per-CTA scratch block in the persistent kernel, which
+// then adds it, in the fixed order of an accumulator chain, into one of a few
+// per-cell accumulators (no atomics, no buffer that grows with the phase
+// space); the staged kernel writes per-group partials for a fixed-order
+// reduction kernel.  The FP32 sweep carries the deviation g = f - M_ref from
+// a per-velocity reference Maxwellian, whose moments are added in FP64 when
+// the sums are formed.  Block faces between stages go through three face
+// planes in global memory indexed by the cell position on the face: a block
+// reads the plane entries written by its upwind neighbour in the previous
+// stage before overwriting them with its own outflow.
 #include <map>
 #include <mutex>
 #include <utility>
@@ -147,7 +152,13 @@ struct SmemLayout {
     static constexpr size_t coef_bytes = align16(sizeof(Real) * SLICE * NCOEF);
     static constexpr size_t vt_bytes = align16(sizeof(Real) * VG * VT);
     static constexpr size_t red_bytes = sizeof(double) * NPART * SLICE;
-    static constexpr size_t fixed = slice_bytes + coef_bytes + vt_bytes + red_bytes;
+    // The halo row of the slice (BX + 1 cell positions) is not read during
+    // the moment phase, so the reduction buffer of the two velocity halves
+    // lives there when it fits (it does for 256 FP32 or 128 FP64 velocities);
+    // a barrier at the end of the slice keeps the next slice's halo from
+    // overwriting it early.
+    static constexpr bool red_in_halo = sizeof(Real) * (BX + 1) * CS >= red_bytes;
+    static constexpr size_t fixed = slice_bytes + coef_bytes + vt_bytes + (red_in_halo ? 0 : red_bytes);
     static int cx_stride(int nxm) { return nxm | 1; }  // odd: conflict-free per-cell reads
     // line: x-lines of LINE nodes keep their c_x in registers (no c_x tables)
     static size_t total(int nxm, bool line)
@@ -215,7 +226,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
     Real *slice = reinterpret_cast<Real *>(smem);
     Real *cs = reinterpret_cast<Real *>(smem + L::slice_bytes);
     Real *vt = reinterpret_cast<Real *>(smem + L::slice_bytes + L::coef_bytes);
-    double *mred = reinterpret_cast<double *>(smem + L::slice_bytes + L::coef_bytes + L::vt_bytes);
+    double *mred = L::red_in_halo ? reinterpret_cast<double *>(smem)
+                                  : reinterpret_cast<double *>(smem + L::slice_bytes + L::coef_bytes + L::vt_bytes);
     const int cxs = nxm | 1;
     Real *xn = reinterpret_cast<Real *>(smem + L::fixed);  // [nxm][2]
     Real *cxh = reinterpret_cast<Real *>(smem + L::fixed + align16(sizeof(Real) * 2 * nxm));  // [SLICE][cxs]
@@ -246,7 +258,11 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
     const int nx = a.nx, ny = a.ny;
     const size_t ncell = a.ncell;
     const size_t Nv = (size_t)a.Nv;
-    const bool any_solid = a.any_solid != 0;
+    // solid cells or solid neighbours in this block (a.blk_plain marks the
+    // physical blocks that have neither; without it every block of a problem
+    // with solid cells counts as having them)
+    const bool any_solid =
+        a.any_solid != 0 && !(a.blk_plain != nullptr && a.blk_plain[((size_t)bzi * a.nby + byi) * a.nbx + bxi] != 0);
 
     auto GX = [&](int li) { return px ? x0 + li : x0 + ex - 1 - li; };
     auto GY = [&](int lj) { return py ? y0 + lj : y0 + ey - 1 - lj; };
@@ -841,6 +857,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 }
             }
         }
+        // the next slice's halo row overwrites the reduction buffer
+        if constexpr (L::red_in_halo) __syncthreads();
     }
 
     // z outflow of the block for the next stage (own velocities only)

@@ -282,6 +282,18 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
     t.nbx = (nx + BX - 1) / BX;
     t.nby = (ny + BY - 1) / BY;
     t.nbz = (nz + t.bz - 1) / t.bz;
+    // blocks without solid cells and without solid neighbours
+    t.blk_plain.clear();
+    if (t.any_solid) {
+        t.blk_plain.assign((size_t)t.nbx * t.nby * t.nbz, 1);
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    const size_t c = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
+                    if (t.solid[c] || (t.side_flags[c] & 63))
+                        t.blk_plain[((size_t)(k / t.bz) * t.nby + j / BY) * t.nbx + i / BX] = 0;
+                }
+    }
     const int n_stages = t.nbx + t.nby + t.nbz - 2;
     std::vector<std::vector<int4>> stages(n_stages);
     for (int o = 0; o < 8; o++) {

@@ -45,6 +45,7 @@ struct HostTables {
     int nbx = 0, nby = 0, nbz = 0;
     std::vector<int> stage_off, stage_n;
     std::vector<int4> work;
+    std::vector<uint8_t> blk_plain;          // [nbz][nby][nbx], problems with solid cells only
     size_t real_bytes() const { return precision == KGS_FP64 ? sizeof(double) : sizeof(float); }
     // Equal cell widths along each axis: the sweep then takes the upwind
     // coefficients a_d = abs(xi_d) / dx_d per velocity (sets a.uniform, a.rd0).

@@ -85,10 +85,11 @@ def test_forward_matches_reference(kgs, channels, shape):
 
 
 # Relative L2 errors of the weight and bias gradients per layer.  Both sides
-# round activations and propagated gradients to bf16, in different orders;
+# use the bf16-rounded weights and stored activations; the CUDA path also
+# stores the propagated gradients in bf16, the reference keeps them in FP64;
 # measured: at most 2.6e-3 on the first two cases, 1.6e-2 on the first layer
-# of the full six-layer network (the rounding differences accumulate over
-# the depth of the backward pass).
+# of the full six-layer network (the gradient roundings accumulate over the
+# depth of the backward pass).
 @pytest.mark.parametrize("channels,shape,masked,tol", [
     ((11, 16, 112, 32, 8), (2, 5, 6, 7), False, 1e-2),
     ((11, 16, 8), (1, 20, 20, 20), True, 1e-2),     # 125 voxel tiles: several weight-gradient chunks
