@@ -33,6 +33,7 @@ class _Problem(ctypes.Structure):
         ("wall_mode", ctypes.c_int),
         ("mass_rescale", ctypes.c_int),
         ("q_lagged", ctypes.c_int),
+        ("order", ctypes.c_int),
     ]
 
 
@@ -111,6 +112,7 @@ class Oracle:
         P.wall_mode = int(prob.wall_mode)
         P.mass_rescale = int(prob.mass_rescale)
         P.q_lagged = int(getattr(prob, "q_lagged", 0))
+        P.order = int(getattr(prob, "order", 1))
         self._P = P
         m0 = None
         if macros0 is not None:

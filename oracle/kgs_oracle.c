@@ -9,7 +9,9 @@
  *   Eq. (2)  Shakhov equilibrium f^S from the lagged macros,
  *   Eq. (6)  outer iteration with f^S and tau lagged at step n,
  *   Eq. (7)  first-order upwind implicit update, swept along the
- *            characteristic direction of each velocity,
+ *            characteristic direction of each velocity (optionally the
+ *            second-order upwind difference that Section 6 names as the
+ *            next step),
  *   Eq. (5)  quadrature moments,
  *   Eq. (8)  diffuse-wall emission with the lagged wall density,
  *   Eq. (9)  wall density from the non-penetration condition,
@@ -22,8 +24,10 @@
  * range order (kgso_set_threads), for comparisons at full workload sizes.
  *
  * Parity status: every function here is pinned by the CPU tests (closed-form
- * quadrature moments, dense linear solves of the sweep, rest state, mass,
- * mirror symmetry, free-molecular linear system, BGK limit).
+ * quadrature moments, dense linear solves of the sweep of either order, the
+ * convergence order of both on a relaxation problem with a closed-form
+ * solution, rest state, mass, mirror symmetry, free-molecular linear system,
+ * BGK limit).
  */
 #include "kgs_oracle.h"
 
@@ -278,6 +282,14 @@ void kgso_sweep(const kgso_state *s, int a, double *f)
                     double coef = fabs(xi[d]) / width[d][ijk[d]];
                     int face = 2 * d + (xi[d] > 0.0 ? 0 : 1); /* upwind side */
                     int n = neighbour(s, c, face);
+                    int n2 = n >= 0 ? neighbour(s, n, face) : -1;
+                    if (p->order == 2 && n2 >= 0) {
+                        /* Second-order upwind (reading of Section 6, no
+                         * limiter): |xi_d| (3 f_c - 4 f_n + f_n2) / (2 dx_d). */
+                        num += coef * (2.0 * f[n] - 0.5 * f[n2]);
+                        den += 1.5 * coef;
+                        continue;
+                    }
                     double up = n >= 0 ? f[n] : kgso_ghost(s, c, face, a);
                     num += coef * up;
                     den += coef;
@@ -372,8 +384,18 @@ static void rho_w_from_flux(kgso_state *s, const double *F)
 kgso_state *kgso_create(const kgso_problem *p, const double *macros0)
 {
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nvx < 1 || p->nvy < 1 || p->nvz < 1) return NULL;
+    if (p->order < 0 || p->order > 2) return NULL;
+    if (p->order == 2) {
+        /* the three-point difference assumes equal widths along each axis */
+        const double *w[3] = {p->dx, p->dy, p->dz};
+        const int n[3] = {p->nx, p->ny, p->nz};
+        for (int d = 0; d < 3; d++)
+            for (int q = 1; q < n[d]; q++)
+                if (w[d][q] != w[d][0]) return NULL;
+    }
     kgso_state *s = (kgso_state *)calloc(1, sizeof(kgso_state));
     s->p = *p;
+    if (s->p.order == 0) s->p.order = 1;
     s->threads = 1;
     s->ncell = p->nx * p->ny * p->nz;
     s->nvel = p->nvx * p->nvy * p->nvz;

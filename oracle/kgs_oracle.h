@@ -43,6 +43,7 @@ typedef struct {
     int wall_mode;                       /* KGSO_WALL_DISCRETE / KGSO_WALL_ANALYTIC */
     int mass_rescale;                    /* 1: keep total mass fixed (Section 3.4) */
     int q_lagged;                        /* 1: heat flux about the lagged U^n      */
+    int order;                           /* upwind order of the sweep: 1 (Eq. (7), also 0) or 2 */
 } kgso_problem;
 
 typedef struct kgso_state kgso_state;
@@ -86,7 +87,9 @@ void kgso_moments(const kgso_state *s, const double *f, double out[8]);
 
 /* The upwind sweep of Eq. (7) for one discrete velocity a, using the state's
  * current macros (for f^S and tau) and wall densities.  out[ncell]; solid cells
- * are set to 0. */
+ * are set to 0.  With order 2 the derivative along an axis is the three-point
+ * backward difference wherever both upwind neighbours are fluid cells (uniform
+ * cell widths per axis only; kgso_create rejects other grids). */
 void kgso_sweep(const kgso_state *s, int a, double *out);
 
 /* The ghost value seen by cell c through its face `face` for velocity a

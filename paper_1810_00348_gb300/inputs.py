@@ -61,6 +61,7 @@ class Problem:
     wall_mode: int = WALL_DISCRETE
     mass_rescale: int = 1
     q_lagged: int = 0                       # 1: heat flux about the lagged U^n (Algorithm 3's moments)
+    order: int = 1                          # upwind order of the sweep: 1 (Eq. (7)) or 2 (three-point)
     name: str = ""
 
     @property

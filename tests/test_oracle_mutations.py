@@ -34,6 +34,12 @@ MUTATIONS = [
      "        Uq = Ulag;", "        Uq = U;"),
     ("incoming wall flux without the quadrature weight",
      "return xn < 0.0 ? w * (-xn) * f : 0.0;", "return xn < 0.0 ? (-xn) * f : 0.0;"),
+    ("second-order stencil with the first-order diagonal",
+     "den += 1.5 * coef;", "den += coef;"),
+    ("second upwind neighbour with the wrong weight",
+     "num += coef * (2.0 * f[n] - 0.5 * f[n2]);", "num += coef * (2.0 * f[n] - 1.0 * f[n2]);"),
+    ("second-order stencil reusing the first upwind neighbour",
+     "int n2 = n >= 0 ? neighbour(s, n, face) : -1;", "int n2 = n;"),
     ("temperature without the kinetic energy subtracted",
      "double T = (rhoE[c] - 0.5 * rho[c] * (u0 * u0 + u1 * u1 + u2 * u2)) / (1.5 * rho[c] * R_GAS);",
      "double T = rhoE[c] / (1.5 * rho[c] * R_GAS);"),

@@ -2,7 +2,9 @@
 
 Each test checks the oracle against something other than itself: closed-form
 moments of Maxwellians (Eqs. (2), (5)), the textbook hard-sphere viscosity
-(Eq. (10) at omega = 1/2), a dense LU solve of the upwind system (Eq. (7)),
+(Eq. (10) at omega = 1/2), a dense LU solve of the upwind system (Eq. (7))
+and of its second-order variant, the convergence order of both on a
+relaxation problem with a closed-form solution,
 the rest state, mass conservation (Section 3.4), the cavity's mirror
 symmetries (Section 4.1), and the free-molecular fixed point obtained by a
 separate power iteration.
@@ -247,6 +249,71 @@ def test_sweep_matches_dense_solve(case):
         np.testing.assert_allclose(f, f_ref, rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("case", ["cube4", "ragged", "solid"])
+def test_second_order_sweep_matches_dense_solve(case):
+    """The order-2 sweep (three-point upwind differences, Section 6's next
+    step) equals an LU solve of the same system assembled row by row."""
+    if case == "cube4":
+        p = inputs.cavity(4, 5, L_v=3.0, lid=0.2, Kn=0.3)
+    elif case == "ragged":
+        p = inputs.cavity([5, 2, 4], [4, 5, 6], L_v=3.0, lid=0.2, Kn=0.7)
+        p.dx = np.full(5, 0.3)
+        p.dy = np.full(2, 0.45)
+        p.dz = np.full(4, 0.2)
+    else:
+        p = inputs.cavity([5, 4, 3], 5, L_v=3.0, lid=0.2, Kn=0.5)
+        p.solid = np.zeros((3, 4, 5), np.uint8)
+        p.solid[1, 1, 2] = 1
+        p.solid[2, 0, 4] = 1
+    p.order = 2
+    mac = inputs.random_macros(p, 21)
+    o = Oracle(p, mac)
+    o.set_rho_w(inputs.random_rho_w(p, 22))
+    xi, _ = brute.velocities(p)
+    rtau = _rtau(o, p, mac)
+    m = mac.reshape(8, -1)
+    nc = p.ncell
+    for a in range(p.nvel):
+        fS = np.array([o.equilibrium(m[:, c])[a] if rtau[c] > 0 else 0.0 for c in range(nc)])
+        f_ref = brute.dense_upwind2_solve(p, xi[a], rtau, fS, lambda c, face: o.ghost(c, face, a))
+        f = o.sweep(a).reshape(-1)
+        np.testing.assert_allclose(f, f_ref, rtol=1e-12, atol=1e-15)
+
+
+def _relaxation_column(n, order):
+    """One velocity (1.5, 0, 0) crossing n cells of width 1/n from a free
+    stream (rho 2, T 1.2) into gas in uniform equilibrium (rho 1, T 1)."""
+    p = inputs.cavity([n, 1, 1], 5, L_v=3.0, lid=0.0, Kn=0.5)
+    p.face_type = [inputs.FACE_INFLOW] * 6
+    p.rho_in, p.T_in, p.U_in = 2.0, 1.2, [0.0, 0.0, 0.0]
+    p.order = order
+    mac = np.zeros((8, 1, 1, n))
+    mac[0], mac[4] = 1.0, 1.0
+    return p, Oracle(p, mac)
+
+
+@pytest.mark.parametrize("order,lo,hi", [(1, 1.8, 2.2), (2, 3.4, 4.6)])
+def test_sweep_converges_at_its_order(order, lo, hi):
+    """xi f' = (S - f)/tau with S and tau uniform has the solution
+    f = S + (g - S) exp(-(x - x_g)/(xi tau)); the ghost g enters as the value
+    one cell upwind of the first cell (x_g = -dx/2).  Halving dx halves the
+    first-order error and quarters the second-order one."""
+    xi = np.array([1.5, 0.0, 0.0])
+    errs = []
+    for n in (32, 64, 128):
+        p, o = _relaxation_column(n, order)
+        v, _ = brute.velocities(p)
+        a = int(np.flatnonzero((v == xi).all(axis=1))[0])
+        S = brute.maxwellian(1.0, [0, 0, 0], 1.0, xi)
+        g = brute.maxwellian(2.0, [0, 0, 0], 1.2, xi)
+        tau = o.mu_ref() / 0.5  # mu / (rho R T) at rho = T = 1
+        x = (np.arange(n) + 0.5) / n
+        exact = S + (g - S) * np.exp(-(x + 0.5 / n) / (xi[0] * tau))
+        errs.append(np.abs(o.sweep(a).reshape(-1) - exact).max() / abs(g - S))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert lo < r1 < hi and lo < r2 < hi, (errs, r1, r2)
+
+
 def test_sweep_is_a_convex_combination():
     """Maximum principle of the implicit upwind update: each f lies between
     the smallest and largest of the ghosts and f^S values it mixes."""
@@ -265,10 +332,12 @@ def test_sweep_is_a_convex_combination():
 # ---------------------------------------------------------------------------
 # whole iterations: invariants
 
-def test_rest_state_stays_at_rest():
+@pytest.mark.parametrize("order", [1, 2])
+def test_rest_state_stays_at_rest(order):
     """Gas at rest between walls at its own temperature stays at rest to
-    1e-12 (24 nodes on [-6, 6], discrete walls)."""
+    1e-12 (24 nodes on [-6, 6], discrete walls), for either upwind order."""
     p = inputs.cavity(4, 24, L_v=6.0, lid=0.0, Kn=0.5)
+    p.order = order
     o = Oracle(p)
     o.iterate(6)
     m = o.macros()
