@@ -43,7 +43,8 @@ __global__ void coef_kernel(const double *__restrict__ mac, const uint8_t *__res
         const double p = rho * RT;
         // tau = mu / p, mu = mu_ref T^omega (Sections 2.1 and 4)
         const double rtau = p / (mu_ref * pow(T, omega));
-        const double A = rho / pow(2.0 * M_PI * RT, 1.5);
+        const double tpr = 2.0 * M_PI * RT;
+        const double A = rho / (tpr * sqrt(tpr));  // rho (2 pi R T)^(-3/2)
         const double sh = (1.0 - Pr) / (5.0 * p * RT);
         // centre U^n in the sweep precision, stored doubled and negated (exact)
         const double U[3] = {(double)(Real)mac[1 * ncell + c], (double)(Real)mac[2 * ncell + c],
@@ -106,42 +107,90 @@ struct FFSum {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// Sum w M_ref (xi_x - Ux)^a (xi_y - Uy)^b (xi_z - Uz)^c of the reference
+// Sum w M_ref (xi_x - Ux)^A (xi_y - Uy)^B (xi_z - Uz)^C of the reference
 // Maxwellian over the swept velocities: the binomial expansion of its raw
-// moments about the cell's lagged velocity U.
-__device__ double ref_central(const RefMoments &r, int a, int b, int c, const double U[3])
+// moments about the cell's lagged velocity U (compile-time orders, so the
+// loops unroll and the raw moments are read at constant offsets).
+__host__ __device__ constexpr double binom3(int n, int k) { return (k == 0 || k == n) ? 1.0 : (n == 2 ? 2.0 : 3.0); }
+
+template <int A, int B, int C>
+__device__ __forceinline__ double ref_central(const RefMoments &r, const double U[3])
 {
-    const double binom[4][4] = {{1, 0, 0, 0}, {1, 1, 0, 0}, {1, 2, 1, 0}, {1, 3, 3, 1}};
     double s = 0.0;
-    for (int i = 0; i <= a; i++)
-        for (int j = 0; j <= b; j++)
-            for (int k = 0; k <= c; k++) {
-                double f = binom[a][i] * binom[b][j] * binom[c][k];
-                for (int e = i; e < a; e++) f *= -U[0];
-                for (int e = j; e < b; e++) f *= -U[1];
-                for (int e = k; e < c; e++) f *= -U[2];
+#pragma unroll
+    for (int i = 0; i <= A; i++)
+#pragma unroll
+        for (int j = 0; j <= B; j++)
+#pragma unroll
+            for (int k = 0; k <= C; k++) {
+                double f = binom3(A, i) * binom3(B, j) * binom3(C, k);
+#pragma unroll
+                for (int e = i; e < A; e++) f *= -U[0];
+#pragma unroll
+                for (int e = j; e < B; e++) f *= -U[1];
+#pragma unroll
+                for (int e = k; e < C; e++) f *= -U[2];
                 s += f * r.raw[ref_index(i, j, k)];
             }
     return s;
 }
 
 // The reference Maxwellian's part of sum slot q (< SUM_F0) about U.
+template <int Q>
+__device__ __forceinline__ double ref_slot_of(const RefMoments &r, const double U[3])
+{
+    switch (Q) {
+    case P_S0: return ref_central<0, 0, 0>(r, U);
+    case P_S1X: return ref_central<1, 0, 0>(r, U);
+    case P_S1Y: return ref_central<0, 1, 0>(r, U);
+    case P_S1Z: return ref_central<0, 0, 1>(r, U);
+    case P_S2XX: return ref_central<2, 0, 0>(r, U);
+    case P_S2YY: return ref_central<0, 2, 0>(r, U);
+    case P_S2ZZ: return ref_central<0, 0, 2>(r, U);
+    case P_S2XY: return ref_central<1, 1, 0>(r, U);
+    case P_S2XZ: return ref_central<1, 0, 1>(r, U);
+    case P_S2YZ: return ref_central<0, 1, 1>(r, U);
+    case P_S3X: return ref_central<3, 0, 0>(r, U) + ref_central<1, 2, 0>(r, U) + ref_central<1, 0, 2>(r, U);
+    case P_S3Y: return ref_central<2, 1, 0>(r, U) + ref_central<0, 3, 0>(r, U) + ref_central<0, 1, 2>(r, U);
+    default: return ref_central<2, 0, 1>(r, U) + ref_central<0, 2, 1>(r, U) + ref_central<0, 0, 3>(r, U);
+    }
+}
+
+// All 13 reference parts of one cell.
+__device__ __forceinline__ void ref_slots(const RefMoments &r, const double U[3], double (&out)[SUM_F0])
+{
+    out[P_S0] = ref_slot_of<P_S0>(r, U);
+    out[P_S1X] = ref_slot_of<P_S1X>(r, U);
+    out[P_S1Y] = ref_slot_of<P_S1Y>(r, U);
+    out[P_S1Z] = ref_slot_of<P_S1Z>(r, U);
+    out[P_S2XX] = ref_slot_of<P_S2XX>(r, U);
+    out[P_S2YY] = ref_slot_of<P_S2YY>(r, U);
+    out[P_S2ZZ] = ref_slot_of<P_S2ZZ>(r, U);
+    out[P_S2XY] = ref_slot_of<P_S2XY>(r, U);
+    out[P_S2XZ] = ref_slot_of<P_S2XZ>(r, U);
+    out[P_S2YZ] = ref_slot_of<P_S2YZ>(r, U);
+    out[P_S3X] = ref_slot_of<P_S3X>(r, U);
+    out[P_S3Y] = ref_slot_of<P_S3Y>(r, U);
+    out[P_S3Z] = ref_slot_of<P_S3Z>(r, U);
+}
+
+// Runtime slot index (the staged path's (cell, slot) threads).
 __device__ double ref_slot(const RefMoments &r, int q, const double U[3])
 {
     switch (q) {
-    case P_S0: return ref_central(r, 0, 0, 0, U);
-    case P_S1X: return ref_central(r, 1, 0, 0, U);
-    case P_S1Y: return ref_central(r, 0, 1, 0, U);
-    case P_S1Z: return ref_central(r, 0, 0, 1, U);
-    case P_S2XX: return ref_central(r, 2, 0, 0, U);
-    case P_S2YY: return ref_central(r, 0, 2, 0, U);
-    case P_S2ZZ: return ref_central(r, 0, 0, 2, U);
-    case P_S2XY: return ref_central(r, 1, 1, 0, U);
-    case P_S2XZ: return ref_central(r, 1, 0, 1, U);
-    case P_S2YZ: return ref_central(r, 0, 1, 1, U);
-    case P_S3X: return ref_central(r, 3, 0, 0, U) + ref_central(r, 1, 2, 0, U) + ref_central(r, 1, 0, 2, U);
-    case P_S3Y: return ref_central(r, 2, 1, 0, U) + ref_central(r, 0, 3, 0, U) + ref_central(r, 0, 1, 2, U);
-    default: return ref_central(r, 2, 0, 1, U) + ref_central(r, 0, 2, 1, U) + ref_central(r, 0, 0, 3, U);
+    case P_S0: return ref_slot_of<P_S0>(r, U);
+    case P_S1X: return ref_slot_of<P_S1X>(r, U);
+    case P_S1Y: return ref_slot_of<P_S1Y>(r, U);
+    case P_S1Z: return ref_slot_of<P_S1Z>(r, U);
+    case P_S2XX: return ref_slot_of<P_S2XX>(r, U);
+    case P_S2YY: return ref_slot_of<P_S2YY>(r, U);
+    case P_S2ZZ: return ref_slot_of<P_S2ZZ>(r, U);
+    case P_S2XY: return ref_slot_of<P_S2XY>(r, U);
+    case P_S2XZ: return ref_slot_of<P_S2XZ>(r, U);
+    case P_S2YZ: return ref_slot_of<P_S2YZ>(r, U);
+    case P_S3X: return ref_slot_of<P_S3X>(r, U);
+    case P_S3Y: return ref_slot_of<P_S3Y>(r, U);
+    default: return ref_slot_of<P_S3Z>(r, U);
     }
 }
 
@@ -250,52 +299,82 @@ __global__ void __launch_bounds__(CLOSE_CELLS * NPART) part_sums_kernel(const Pa
     }
 }
 
-// Per-cell sums of the persistent sweep's ordered accumulators: thread
-// (cell, slot) adds the nacc accumulators of its slot in accumulator order
-// (float-float for the FP32 path) and writes the FP64 sum.
+// Per-cell sums of the persistent sweep's ordered accumulators, ACC_CELLS
+// cells per block.  First the block's (cell, slot) pairs in address order
+// (coalesced): each adds its slot's nacc accumulators in accumulator order
+// (float-float for the FP32 path) into shared memory.  Then one thread per
+// cell maps the accumulator slots to the NSUM sum slots, adds the reference
+// Maxwellian's part (FP32 path) and writes the FP64 sums.
+constexpr int ACC_CELLS = 128;
 template <typename Real>
-__global__ void __launch_bounds__(256) acc_sums_kernel(const AccSumArgs a)
+__global__ void __launch_bounds__(ACC_CELLS) acc_sums_kernel(const AccSumArgs a)
 {
+    __shared__ double tot[ACC_CELLS * ACC_SPLIT];
     const size_t ncell = a.ncell;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncell * NSUM) return;
-    const size_t c = i / NSUM;
-    const int q = (int)(i % NSUM);
-    const int side = q - SUM_F0;
-    // the accumulator slot of sum slot q (compact layout: the flux of an axis
-    // belongs to the side that has a wall, zero on the other side)
-    int slot = q;
-    bool zero = false;
-    if (side >= 0 && a.acc_slots == ACC_COMPACT) {
-        slot = SUM_F0 + side / 2;
-        zero = a.wall_kind[(size_t)side * ncell + c] < 0;
-    }
-    double v = 0.0;
-    if (!(a.solid && a.solid[c]) && !zero) {
-        const size_t at = c * a.acc_slots + slot, ks = ncell * a.acc_slots;
+    const size_t c0 = (size_t)blockIdx.x * ACC_CELLS;
+    const int nc = (int)min((size_t)ACC_CELLS, ncell - c0);
+    const int ns = a.acc_slots, nacc = a.nacc;
+    const size_t ks = ncell * ns;
+    for (int j = threadIdx.x; j < nc * ns; j += ACC_CELLS) {
+        const size_t at = c0 * ns + j;
         if (sizeof(Real) == 8) {
             const double *p = static_cast<const double *>(a.acc) + at;
-            for (int k = 0; k < a.nacc; k++) v += p[(size_t)k * ks];
+            double e[NACC_MAX];
+#pragma unroll
+            for (int k = 0; k < NACC_MAX; k++) e[k] = k < nacc ? p[(size_t)k * ks] : 0.0;
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < NACC_MAX; k++)
+                if (k < nacc) v += e[k];
+            tot[j] = v;
         } else {
             const float2 *p = static_cast<const float2 *>(a.acc) + at;
+            float2 e[NACC_MAX];
+#pragma unroll
+            for (int k = 0; k < NACC_MAX; k++) e[k] = k < nacc ? p[(size_t)k * ks] : make_float2(0.f, 0.f);
             FFSum t;
-            for (int k = 0; k < a.nacc; k++) {
-                const float2 e = p[(size_t)k * ks];
-                t.add(e.x, 0.f);
-                t.add(e.y, 0.f);
-            }
-            v = t.value();
-            // the FP32 sweep summed g = f - M_ref: add the reference's part
-            if (q < SUM_F0) {
-                double U[3];
-                centre32(a.coef, c, U);
-                v += ref_slot(a.ref, q, U);
-            } else if (a.wall_kind[(size_t)side * ncell + c] >= 0) {
-                v += a.ref.flux[side];
-            }
+#pragma unroll
+            for (int k = 0; k < NACC_MAX; k++)
+                if (k < nacc) {
+                    t.add(e[k].x, 0.f);
+                    t.add(e[k].y, 0.f);
+                }
+            tot[j] = t.value();
         }
     }
-    a.sums[(size_t)q * ncell + c] = v;
+    __syncthreads();
+    const int cl = threadIdx.x;
+    if (cl >= nc) return;
+    const size_t c = c0 + cl;
+    const double *tc = tot + (size_t)cl * ns;
+    if (a.solid && a.solid[c]) {
+        for (int q = 0; q < NSUM; q++) a.sums[(size_t)q * ncell + c] = 0.0;
+        return;
+    }
+    if constexpr (sizeof(Real) == 4) {
+        // the FP32 sweep summed g = f - M_ref: add the reference's part
+        double U[3], ref[SUM_F0];
+        centre32(a.coef, c, U);
+        ref_slots(a.ref, U, ref);
+#pragma unroll
+        for (int q = 0; q < SUM_F0; q++) a.sums[(size_t)q * ncell + c] = tc[q] + ref[q];
+    } else {
+        for (int q = 0; q < SUM_F0; q++) a.sums[(size_t)q * ncell + c] = tc[q];
+    }
+#pragma unroll
+    for (int side = 0; side < 6; side++) {
+        // compact layout: the flux of an axis belongs to the side that has a
+        // wall, zero on the other side
+        const bool wall = a.wall_kind[(size_t)side * ncell + c] >= 0;
+        double v;
+        if (ns == ACC_COMPACT)
+            v = wall ? tc[SUM_F0 + side / 2] : 0.0;
+        else
+            v = tc[SUM_F0 + side];
+        if constexpr (sizeof(Real) == 4)
+            if (wall) v += a.ref.flux[side];
+        a.sums[(size_t)(SUM_F0 + side) * ncell + c] = v;
+    }
 }
 
 // Closure of one outer iteration, one thread per cell (CLOSE_CELLS cells per
@@ -576,11 +655,11 @@ cudaError_t launch_part_sums(const PartSumArgs &a, cudaStream_t s)
 
 cudaError_t launch_acc_sums(const AccSumArgs &a, cudaStream_t s)
 {
-    const unsigned nb = nblk((size_t)a.ncell * NSUM, 256);
+    const unsigned nb = nblk((size_t)a.ncell, ACC_CELLS);
     if (a.precision == 0)
-        acc_sums_kernel<double><<<nb, 256, 0, s>>>(a);
+        acc_sums_kernel<double><<<nb, ACC_CELLS, 0, s>>>(a);
     else
-        acc_sums_kernel<float><<<nb, 256, 0, s>>>(a);
+        acc_sums_kernel<float><<<nb, ACC_CELLS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
