@@ -39,6 +39,10 @@ N_CELL, N_VEL, KN, LID = 64, 32, 1.0, 0.16
 # (FMA = 2): equilibrium of Eq. (2) 20 + exp 1; implicit update of Eq. (7)
 # 13 (with the division); 13 moment sums about U^n 34.
 FLOPS_PER_PP = 68
+# The second-order sweep adds three extrapolated upwind values
+# h_d = f_1 + (f_1 - f_2)/3 (a subtraction and an FMA each) and the scaled
+# coefficients 3 a_d / 2.
+FLOPS_PER_PP_ORDER2 = FLOPS_PER_PP + 9 + 3
 # dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch (ncu, 32^3
 # cells x 32^3 velocities, 256 velocities per CTA, blocks 8x8x32): 2.897e9 B
 # over 1.074e9 phase points
@@ -437,6 +441,37 @@ def run_extras(args, kgs, inputs, torch, peaks):
         del c
     except Exception as e:  # noqa: BLE001
         out["cube"] = {"error": repr(e)}
+    try:
+        # the second-order upwind sweep (Section 6's next step) on the
+        # headline cavity: two resident slices, 128 velocities per CTA
+        p = inputs.cavity(N_CELL, N_VEL, Kn=KN, lid=LID)
+        p.order = 2
+        pp = p.phase_points()
+        c = kgs.kgs_setup(p, precision=kgs.KGS_MIXED)
+        kgs.kgs_set_profiling(c, True)
+        kgs.kgs_iterate(c, 3)
+        kgs.kgs_profile(c)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_it = 5
+        ev0.record()
+        rc, _, _ = kgs.kgs_iterate(c, n_it)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        sweep_ms, _, _ = kgs.kgs_profile(c)
+        tflops = FLOPS_PER_PP_ORDER2 * pp / (sweep_ms / n_it / 1e3) / 1e12
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+        out["order2"] = {
+            "workload": WORKLOAD + ", second-order upwind sweep, mixed",
+            "value": pp * n_it / (ms / 1e3), "unit": "phase-point updates/s", "iterations": n_it, "rc": rc,
+            "ms_per_iteration": ms / n_it, "sweep_ms_per_iteration": sweep_ms / n_it,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak, "flops_per_phase_point": FLOPS_PER_PP_ORDER2},
+            "device_bytes": kgs.kgs_info(c)["device_bytes"]}
+        del c
+    except Exception as e:  # noqa: BLE001
+        out["order2"] = {"error": repr(e)}
     if args.paper_cube:
         try:
             # the cube on the paper's stretched mesh (Section 4.2): per-cell

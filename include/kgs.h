@@ -125,7 +125,17 @@ typedef struct {
  *                velocity planes iz in [vz_begin, vz_end) (0, 0 = all).  Its
  *                per-cell sums (kgs_sweep_sums) are then partial; the wall
  *                normalisation and the initial wall densities still use the
- *                whole velocity grid. */
+ *                whole velocity grid.
+ *   order        upwind order of the sweep: 1 (or 0) is Eq. (7).  2 is the
+ *                second-order upwind difference that Section 6 names as the
+ *                next step, read as the three-point backward difference
+ *                (3 f_i - 4 f_{i-1} + f_{i-2}) / (2 dx) along each axis without
+ *                a limiter, used where both upwind cells are in the domain
+ *                (the first two cells from each side keep Eq. (7)).  Order 2
+ *                needs equal cell widths along each axis, no solid cells and
+ *                no free-stream sides, holds two slices and two face planes
+ *                per direction, and sweeps 128 velocities per thread block
+ *                (KGS_EINVAL otherwise). */
 typedef struct {
     int precision;
     int wall_norm;
@@ -137,6 +147,7 @@ typedef struct {
     void *stream;
     int q_lagged;
     int vz_begin, vz_end;
+    int order;
 } kgs_opts;
 
 /* Sizes and counters of a context. */

@@ -274,6 +274,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
 {
     if (!out || n < 1 || !probs || !opts) return KGS_EINVAL;
     *out = nullptr;
+    if (opts->order == 2) return KGS_EINVAL;  // batches sweep at first order
     int vpc = opts->v_per_cta, bz = opts->block_z;
     if (vpc == 0 && bz == 0) {
         // shapes of the largest instance, picked by the autotuner
@@ -323,6 +324,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
         o.wall_norm = p.wall_norm;
         o.mass_rescale = p.mass_rescale;
         o.q_lagged = p.q_lagged;
+        o.order = 1;
         o.v_per_cta = vpc;
         o.block_z = bz;
         int rc = ctx_create(&b->ctx[i], &p.grid, p.solid, &p.vgrid, &p.gas, &p.bc, &o);

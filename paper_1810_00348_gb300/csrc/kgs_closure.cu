@@ -24,7 +24,7 @@ template <typename Real>
 __global__ void coef_kernel(const double *__restrict__ mac, const uint8_t *__restrict__ solid,
                             const uint8_t *__restrict__ side_flags, const double *__restrict__ rdx,
                             const double *__restrict__ rdy, const double *__restrict__ rdz, int nx, int ny, int nz,
-                            double mu_ref, double omega, double Pr, Real *__restrict__ coef)
+                            double mu_ref, double omega, double Pr, int dev_src, Real *__restrict__ coef)
 {
     const size_t ncell = (size_t)nx * ny * nz;
     const size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -70,6 +70,17 @@ __global__ void coef_kernel(const double *__restrict__ mac, const uint8_t *__res
         out[C_RDX] = (Real)rdx[i];
         out[C_RDY] = (Real)rdy[j];
         out[C_RDZ] = (Real)rdz[k];
+        if (dev_src) {
+            // FP32 second-order sweep (uniform grid: the widths are not read
+            // per cell): the base-2 exponent of f^S_M / M_ref, against the
+            // reference at rest (rho = 1, T = 1), is
+            //   D = |xi|^2 (nexp - nexp_ref) + nexp (-2 U.xi) + K,
+            //   nexp - nexp_ref = log2(e) (T - 1) / T,
+            //   K = log2(rho) - 1.5 log2(T) - log2(e) |U|^2 / T,
+            // both small where the gas is near the reference state
+            out[C_RDX] = (Real)(LOG2E * (T - 1.0) / T);
+            out[C_RDY] = (Real)(log2(rho) - 1.5 * log2(T) - LOG2E * U2 / (2.0 * RT));
+        }
     }
     out[C_FLAGS] = flag_value<Real>(flags);
     for (int q = 0; q < NCOEF; q++) coef[c * NCOEF + q] = out[q];
@@ -631,15 +642,15 @@ inline unsigned nblk(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, const uint8_t *side_flags,
                         const double *rdx, const double *rdy, const double *rdz, int nx, int ny, int nz,
-                        double mu_ref, double omega, double Pr, void *coef, cudaStream_t s)
+                        double mu_ref, double omega, double Pr, void *coef, cudaStream_t s, int dev_src)
 {
     const size_t n = (size_t)nx * ny * nz;
     if (precision == 0)
         coef_kernel<double><<<nblk(n, 256), 256, 0, s>>>(mac, solid, side_flags, rdx, rdy, rdz, nx, ny, nz, mu_ref,
-                                                          omega, Pr, static_cast<double *>(coef));
+                                                          omega, Pr, 0, static_cast<double *>(coef));
     else
         coef_kernel<float><<<nblk(n, 256), 256, 0, s>>>(mac, solid, side_flags, rdx, rdy, rdz, nx, ny, nz, mu_ref,
-                                                         omega, Pr, static_cast<float *>(coef));
+                                                         omega, Pr, dev_src, static_cast<float *>(coef));
     return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ struct kgs_ctx {
     double *mac = nullptr, *mac_new = nullptr, *rho_w = nullptr, *rho_w_new = nullptr;
     void *coef = nullptr, *vel = nullptr, *velm = nullptr, *mtab = nullptr, *FX = nullptr, *FY = nullptr,
          *FZ = nullptr;
+    void *FX2 = nullptr, *FY2 = nullptr, *FZ2 = nullptr;  // second face planes of the order-2 sweep
     void *part = nullptr;   // staged sweep only: per-(group, cell) partials
     void *acc = nullptr;    // persistent sweep: ordered accumulators [nacc][ncell][acc_slots]
     int use_acc = 0;        // the sweep runs persistent and adds into acc

@@ -31,7 +31,8 @@ enum {
     C_RTAU,                 // 1/tau
     C_FLAGS,                // cell flags (below), their bits stored in the value (flag_value)
     C_QX, C_QY, C_QZ,       // q' = (1 - Pr) q / (5 p R T)
-    C_RDX, C_RDY, C_RDZ,    // 1/dx_i, 1/dy_j, 1/dz_k
+    C_RDX, C_RDY, C_RDZ,    // 1/dx_i, 1/dy_j, 1/dz_k (FP32 second-order sweep, uniform grid:
+                            // C_RDX, C_RDY hold the exponent terms of its deviation source)
     C_SHK0,                 // |U^n|^2 / (R T) - 5, so that |c|^2/(RT) - 5 = s/(RT) + C_SHK0
     C_MUQ                   // -U^n . q'
 };
@@ -98,7 +99,8 @@ struct SweepArgs {
     const void *vel;              // Real[Nv][4]: xi_x, xi_y, xi_z, w (octant-sorted)
     const void *velm;             // Real[Nv][8]: w_x, w_y w_z, the low parts of xi_x, xi_y, xi_z
                                   // (xi = hi + lo with hi = the value in vel), M_ref (FP32
-                                  // path; 0 for FP64), 2 unused
+                                  // path; 0 for FP64), the rounding error of M_ref (FP32
+                                  // path), 1 unused
     int oct_nx[8];                // x nodes in each octant (length of its velocity x-lines)
     int nxo_max;                  // max over octants of oct_nx
     int any_solid;                // the problem has solid cells
@@ -108,6 +110,8 @@ struct SweepArgs {
     const void *mtab;             // Real[MT_ROWS][Nv]: unit wall Maxwellians, free stream
     int side_inflow[6];           // domain side s is a free-stream boundary
     void *FX, *FY, *FZ;           // face planes: [nz*ny][Nv], [nz*nx][Nv], [ny*nx][Nv]
+    int order;                    // upwind order of the sweep (1: Eq. (7), 2: three-point differences)
+    void *FX2, *FY2, *FZ2;        // order 2: the planes one cell further upwind (same shapes)
     void *part;                   // staged sweep: [n_vg][ncell][NPART], double (FP64 path) or
                                   // float2 (s, c) with value s - c (FP32 path, Kahan pair)
     void *acc;                    // persistent sweep: [nacc][ncell][acc_slots] ordered accumulators
@@ -177,14 +181,16 @@ __host__ __device__ inline double flag_value<double>(int f)
 __device__ __forceinline__ int flag_bits(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int flag_bits(double v) { return (int)__double_as_longlong(v); }
 
+// order: upwind order of the sweep; order 2 exists for tv = 1 on uniform
+// grids only (0 CTAs per SM / cudaErrorInvalidValue otherwise).
 cudaError_t launch_sweep_persistent(int precision, int tv, int line16, int uniform, const BatchSweepArgs &b, int nxo_max,
-                                    int grid, cudaStream_t s);
+                                    int grid, cudaStream_t s, int order = 1);
 // Resident CTAs per SM of the persistent kernel (also sets its shared-memory limit).
-int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem);
+int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem, int order = 1);
 
-// Sweep launch (one wavefront stage).  precision: 0 FP64, 1 FP32.
+// Sweep launch (one wavefront stage, order 1).  precision: 0 FP64, 1 FP32.
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s);
-size_t sweep_smem_bytes(int precision, int tv, int line16, int nxo_max);
+size_t sweep_smem_bytes(int precision, int tv, int line16, int nxo_max, int order = 1);
 
 // Per-cell sums of the staged sweep's per-group partials (fixed group order).
 struct PartSumArgs {
@@ -216,9 +222,11 @@ struct ClosureArgs {
     double *blk_mass;             // [close_blocks(ncell)]
 };
 
+// dev_src (FP32 only): the C_RDX / C_RDY slots carry the exponent terms of
+// the second-order sweep's deviation source instead of 1/dx, 1/dy.
 cudaError_t launch_coef(int precision, const double *mac, const uint8_t *solid, const uint8_t *cell_flags_side,
                         const double *rdx, const double *rdy, const double *rdz, int nx, int ny, int nz,
-                        double mu_ref, double omega, double Pr, void *coef, cudaStream_t s);
+                        double mu_ref, double omega, double Pr, void *coef, cudaStream_t s, int dev_src = 0);
 // Cells per block of the closure kernel; blk_mass holds close_blocks(ncell)
 // values.
 constexpr int CLOSE_CELLS = 32;

@@ -167,6 +167,10 @@ SweepArgs kgs::ctx_sweep_args(const kgs_ctx *c)
     a.FX = c->FX;
     a.FY = c->FY;
     a.FZ = c->FZ;
+    a.order = t.order;
+    a.FX2 = c->FX2;
+    a.FY2 = c->FY2;
+    a.FZ2 = c->FZ2;
     a.part = c->part;
     a.acc = c->acc;
     a.nacc = t.nacc;
@@ -184,7 +188,7 @@ int kgs::ctx_launch_coef(kgs_ctx *c)
 {
     const HostTables &t = c->t;
     KGS_CHECK(launch_coef(t.precision, c->mac, c->solid, c->side_flags, c->rdx, c->rdy, c->rdz, t.nx, t.ny, t.nz,
-                          t.mu_ref, t.omega, t.Pr, c->coef, c->stream));
+                          t.mu_ref, t.omega, t.Pr, c->coef, c->stream, t.order == 2 && t.precision == KGS_MIXED));
     c->kernel_launches += 1;
     return KGS_OK;
 }
@@ -217,7 +221,8 @@ int kgs::ctx_launch_stages(kgs_ctx *c)
         ba.skip_publish = -1;
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[0], st));
         KGS_CHECK(
-            launch_sweep_persistent(t.precision, t.tv, a.line16, a.uniform, ba, t.nxo_max, c->persist_grid, st));
+            launch_sweep_persistent(t.precision, t.tv, a.line16, a.uniform, ba, t.nxo_max, c->persist_grid, st,
+                                    t.order));
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[1], st));
         c->kernel_launches += 1;
         c->sweep_launches += 1;
@@ -289,7 +294,10 @@ int kgs::ctx_persist_init(kgs_ctx *c)
     KGS_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
     const SweepArgs a = ctx_sweep_args(c);
     const int per_sm = sweep_persistent_occupancy(t.precision, t.tv, a.line16, a.uniform,
-                                                  sweep_smem_bytes(t.precision, t.tv, a.line16, t.nxo_max));
+                                                  sweep_smem_bytes(t.precision, t.tv, a.line16, t.nxo_max, t.order),
+                                                  t.order);
+    // the second-order sweep exists only as the persistent kernel
+    if (per_sm < 1 && t.order == 2) return KGS_EINVAL;
     if (per_sm < 1) {
         // the launch per stage, with per-group partials
         return dalloc(c, &c->part, (size_t)t.n_vg * NPART * t.ncell * 8);
@@ -443,7 +451,7 @@ int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const k
     if (!out || !opts) return KGS_EINVAL;
     *out = nullptr;
     int rc = validate_problem(grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta,
-                              opts->block_z, opts->vz_begin, opts->vz_end);
+                              opts->block_z, opts->vz_begin, opts->vz_end, opts->order);
     if (rc) return rc;
     (void)cudaGetLastError();  // launches below check their own status
     if ((rc = ctx_create(out, grid, solid, vg, gas, bc, opts))) return rc;
@@ -476,7 +484,7 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
     c->tol = opts->tol > 0.0 ? opts->tol : 1e-8;
     HostTables &t = c->t;
     build_tables(t, grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta, opts->block_z,
-                 opts->vz_begin, opts->vz_end);
+                 opts->vz_begin, opts->vz_end, opts->order);
     c->q_lagged = opts->q_lagged ? 1 : 0;
     const size_t n = t.ncell;
     const size_t rsz = t.real_bytes();
@@ -508,10 +516,18 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
     }
     if (t.any_solid && ((rc = upload(c, &c->solid, t.solid)) || (rc = upload(c, &c->blk_plain, t.blk_plain))))
         return fail(rc);
+    if (t.order == 2 && ((rc = dalloc(c, &c->FX2, (size_t)t.nz * t.ny * t.Nv * rsz)) ||
+                         (rc = dalloc(c, &c->FY2, (size_t)t.nz * t.nx * t.Nv * rsz)) ||
+                         (rc = dalloc(c, &c->FZ2, (size_t)t.ny * t.nx * t.Nv * rsz))))
+        return fail(rc);
     if (cudaMemset(c->FX, 0, (size_t)t.nz * t.ny * t.Nv * rsz) != cudaSuccess ||
         cudaMemset(c->FY, 0, (size_t)t.nz * t.nx * t.Nv * rsz) != cudaSuccess ||
         cudaMemset(c->FZ, 0, (size_t)t.ny * t.nx * t.Nv * rsz) != cudaSuccess ||
         cudaMemset(c->coef, 0, n * NCOEF * rsz) != cudaSuccess)
+        return fail(KGS_ECUDA);
+    if (t.order == 2 && (cudaMemset(c->FX2, 0, (size_t)t.nz * t.ny * t.Nv * rsz) != cudaSuccess ||
+                         cudaMemset(c->FY2, 0, (size_t)t.nz * t.nx * t.Nv * rsz) != cudaSuccess ||
+                         cudaMemset(c->FZ2, 0, (size_t)t.ny * t.nx * t.Nv * rsz) != cudaSuccess))
         return fail(KGS_ECUDA);
     if (cudaMallocHost(&c->h_resid, 3 * sizeof(double)) != cudaSuccess) return fail(KGS_ENOMEM);
     if (cudaMemset(c->resid, 0, 3 * sizeof(double)) != cudaSuccess) return fail(KGS_ECUDA);

@@ -73,6 +73,21 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// 2^x - 1 with a relative error near FP32 rounding also for small x: for
+// |x| < 1/4 the Taylor series of e^y - 1 in y = x ln 2 up to y^6 (the first
+// omitted term is below 6e-9 of the sum), else the hardware 2^x minus 1
+// (no cancellation beyond three bits there).
+__device__ __forceinline__ float exp2m1(float x)
+{
+    const float y = x * 0.693147180559945309f;
+    float p = fmaf(y, 1.f / 720.f, 1.f / 120.f);
+    p = fmaf(p, y, 1.f / 24.f);
+    p = fmaf(p, y, 1.f / 6.f);
+    p = fmaf(p, y, 0.5f);
+    const float small = fmaf(y * y, p, y);
+    return fabsf(x) < 0.25f ? small : ex2_approx(x) - 1.f;
+}
+
 // exp of the scaled exponent: FP64 uses exp(), FP32 the hardware 2^x with the
 // log2(e) factor already folded into the coefficient C_NEXP.
 __device__ __forceinline__ double eq_exp(double x) { return exp(x); }
@@ -144,21 +159,28 @@ __device__ __forceinline__ Quad<double> load_quad(const double *p)
     return {a.x, a.y, b.x, b.y};
 }
 
-template <typename Real, int TV>
+template <typename Real, int TV, int ORDER = 1>
 struct SmemLayout {
     static constexpr int VG = NT * TV;
     static constexpr int CS = VG + 1;  // odd cell stride: conflict-free per-cell reads
-    static constexpr size_t slice_bytes = align16(sizeof(Real) * (BY + 1) * (BX + 1) * CS);
+    static constexpr int H = ORDER;    // halo width: the upwind cells a stencil reaches
+    static constexpr int PX = BX + H;  // slice positions per row, halo included
+    static constexpr size_t slice_bytes = align16(sizeof(Real) * (BY + H) * PX * CS);
+    // order 2: slice k-2 at the block's own cells
+    static constexpr size_t slice2_bytes = ORDER == 2 ? align16(sizeof(Real) * BY * BX * CS) : 0;
     static constexpr size_t coef_bytes = align16(sizeof(Real) * SLICE * NCOEF);
     static constexpr size_t vt_bytes = align16(sizeof(Real) * VG * VT);
     static constexpr size_t red_bytes = sizeof(double) * NPART * SLICE;
-    // The halo row of the slice (BX + 1 cell positions) is not read during
-    // the moment phase, so the reduction buffer of the two velocity halves
-    // lives there when it fits (it does for 256 FP32 or 128 FP64 velocities);
-    // a barrier at the end of the slice keeps the next slice's halo from
-    // overwriting it early.
-    static constexpr bool red_in_halo = sizeof(Real) * (BX + 1) * CS >= red_bytes;
-    static constexpr size_t fixed = slice_bytes + coef_bytes + vt_bytes + (red_in_halo ? 0 : red_bytes);
+    // The halo rows of the slice (H rows of PX cell positions) are not read
+    // during the moment phase, so the reduction buffer of the two velocity
+    // halves lives there when it fits (it does for 256 FP32 or 128 FP64
+    // velocities); a barrier at the end of the slice keeps the next slice's
+    // halo from overwriting it early.
+    static constexpr bool red_in_halo = sizeof(Real) * H * PX * CS >= red_bytes;
+    static constexpr size_t off_coef = slice_bytes + slice2_bytes;
+    static constexpr size_t off_vt = off_coef + coef_bytes;
+    static constexpr size_t off_red = off_vt + vt_bytes;
+    static constexpr size_t fixed = off_red + (red_in_halo ? 0 : red_bytes);
     static int cx_stride(int nxm) { return nxm | 1; }  // odd: conflict-free per-cell reads
     // line: x-lines of LINE nodes keep their c_x in registers (no c_x tables)
     static size_t total(int nxm, bool line)
@@ -215,19 +237,24 @@ __device__ __forceinline__ Real ld_face(const Real *p)
 // COHERENT false) or, in the persistent sweep, to this CTA's scratch block
 // [bz * SLICE][NPART] indexed by the cell's place in the block, from where
 // chain_add moves them into the ordered accumulators.
-template <typename Real, int TV, int LINE, bool COHERENT, bool UNIF>
+//
+// ORDER 2 (second-order upwind, single contexts on solid-free uniform grids):
+// slice2 keeps slice k-2 at the block's cells, the halo is two cells wide,
+// and FX2/FY2/FZ2 carry the block outflow one cell further upwind.
+template <typename Real, int TV, int LINE, bool COHERENT, bool UNIF, int ORDER = 1>
 __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, const int vgy, unsigned char *smem,
                                            void *scratch)
 {
-    using L = SmemLayout<Real, TV>;
+    using L = SmemLayout<Real, TV, ORDER>;
     constexpr int VG = L::VG;
     constexpr int CS = L::CS;
+    constexpr int H = L::H, PX = L::PX;
     const int nxm = a.nxo_max;
     Real *slice = reinterpret_cast<Real *>(smem);
-    Real *cs = reinterpret_cast<Real *>(smem + L::slice_bytes);
-    Real *vt = reinterpret_cast<Real *>(smem + L::slice_bytes + L::coef_bytes);
-    double *mred = L::red_in_halo ? reinterpret_cast<double *>(smem)
-                                  : reinterpret_cast<double *>(smem + L::slice_bytes + L::coef_bytes + L::vt_bytes);
+    Real *slice2 = reinterpret_cast<Real *>(smem + L::slice_bytes);  // order 2 only
+    Real *cs = reinterpret_cast<Real *>(smem + L::off_coef);
+    Real *vt = reinterpret_cast<Real *>(smem + L::off_vt);
+    double *mred = L::red_in_halo ? reinterpret_cast<double *>(smem) : reinterpret_cast<double *>(smem + L::off_red);
     const int cxs = nxm | 1;
     Real *xn = reinterpret_cast<Real *>(smem + L::fixed);  // [nxm][2]
     Real *cxh = reinterpret_cast<Real *>(smem + L::fixed + align16(sizeof(Real) * 2 * nxm));  // [SLICE][cxs]
@@ -267,7 +294,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
     auto GX = [&](int li) { return px ? x0 + li : x0 + ex - 1 - li; };
     auto GY = [&](int lj) { return py ? y0 + lj : y0 + ey - 1 - lj; };
     auto GZ = [&](int lk) { return pz ? z0 + lk : z0 + ez - 1 - lk; };
-    auto SL = [&](int li, int lj) { return ((lj + 1) * (BX + 1) + (li + 1)) * CS; };  // li, lj may be -1
+    auto SL = [&](int li, int lj) { return ((lj + H) * PX + (li + H)) * CS; };  // li, lj may be -1 (-2: order 2)
     auto CELL = [&](int x, int y, int z) { return (size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z); };
 
     const Real *vel = static_cast<const Real *>(a.vel);
@@ -277,12 +304,19 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
     Real *FXp = static_cast<Real *>(a.FX);
     Real *FYp = static_cast<Real *>(a.FY);
     Real *FZp = static_cast<Real *>(a.FZ);
+    Real *FX2p = static_cast<Real *>(a.FX2);
+    Real *FY2p = static_cast<Real *>(a.FY2);
+    Real *FZ2p = static_cast<Real *>(a.FZ2);
+    // order 2: index of the block's first cell along each sweep direction
+    // (cells with index >= 2 have both upwind neighbours in the domain)
+    const int sx0 = px ? x0 : nx - x0 - ex, sy0 = py ? y0 : ny - y0 - ey, sz0 = pz ? z0 : a.nz - z0 - ez;
 
     // ---- per-thread velocities (vl = t + m*NT) and the moment-phase tables ----
     // The FP32 sweep carries g = f - M_ref (mref: the reference Maxwellian of
     // the velocity); every ghost value enters as ghost - M_ref and the source
     // as f^S/tau - M_ref/tau.  The FP64 sweep carries f (mref unused).
     Real xi[TV][3], axi[TV][3], mgx[TV], mgy[TV], mgz[TV], msol[TV], mref[TV];
+    Real dmref[ORDER == 2 ? TV : 1];  // order 2, FP32: the rounding error of M_ref
     size_t gv[TV];
     bool ok[TV];
     const int rowx = a.side_inflow[sidex] ? MT_INFLOW : sidex;
@@ -314,6 +348,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         mgz[m] = mt[(size_t)rowz * Nv + gv[m]];
         msol[m] = mt[(size_t)MT_SOLID * Nv + gv[m]];
         mref[m] = sizeof(Real) == 4 ? velm[gv[m] * 8 + 5] : Real(0);
+        if constexpr (ORDER == 2) dmref[m] = sizeof(Real) == 4 ? velm[gv[m] * 8 + 6] : Real(0);
     }
     // ghost value rho_w * (unit wall or free-stream Maxwellian), as carried
     auto ghost = [&](Real rw, Real mg, int m) -> Real {
@@ -359,6 +394,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
     // ---- prefetch registers: coefficients and halos of one slice ----
     Real pc[CPF];
     Real phx[BY][TV], phy[BX][TV];
+    Real phx2[ORDER == 2 ? BY : 1][TV], phy2[ORDER == 2 ? BX : 1][TV];  // order 2: second halo column / row
     auto prefetch = [&](int lk) {
         const int z = GZ(lk);
         const int cl = (t * CPF) / NCOEF, q0 = (t * CPF) % NCOEF;
@@ -389,6 +425,16 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 for (int m = 0; m < TV; m++)
                     phx[lj2][m] = ok[m] ? ld_face<COHERENT>(fi + lj2 * step + (long long)gv[m]) : Real(0);
             }
+            if constexpr (ORDER == 2) {
+                const Real *fi2 = FX2p + ((size_t)z * ny + GY(0)) * Nv;
+#pragma unroll
+                for (int lj2 = 0; lj2 < BY; lj2++) {
+                    if (lj2 >= ey) break;
+#pragma unroll
+                    for (int m = 0; m < TV; m++)
+                        phx2[lj2][m] = ok[m] ? ld_face<COHERENT>(fi2 + lj2 * step + (long long)gv[m]) : Real(0);
+                }
+            }
         }
         if (yfirst) {
 #pragma unroll
@@ -407,6 +453,16 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
 #pragma unroll
                 for (int m = 0; m < TV; m++)
                     phy[li2][m] = ok[m] ? ld_face<COHERENT>(fi + li2 * step + (long long)gv[m]) : Real(0);
+            }
+            if constexpr (ORDER == 2) {
+                const Real *fi2 = FY2p + ((size_t)z * nx + GX(0)) * Nv;
+#pragma unroll
+                for (int li2 = 0; li2 < BX; li2++) {
+                    if (li2 >= ex) break;
+#pragma unroll
+                    for (int m = 0; m < TV; m++)
+                        phy2[li2][m] = ok[m] ? ld_face<COHERENT>(fi2 + li2 * step + (long long)gv[m]) : Real(0);
+                }
             }
         }
     };
@@ -442,6 +498,24 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 for (int m = 0; m < TV; m++)
                     if (ok[m]) slice[SL(li, lj) + t + m * NT] = v[li][m];
             }
+            if constexpr (ORDER == 2) {
+                // slice k0-2 (the upwind block's second-last slice)
+                const Real *fi2 = FZ2p + ((size_t)GY(lj) * nx + GX(0)) * Nv;
+#pragma unroll
+                for (int li = 0; li < BX; li++) {
+                    if (li >= ex) break;
+#pragma unroll
+                    for (int m = 0; m < TV; m++)
+                        v[li][m] = ok[m] ? ld_face<COHERENT>(fi2 + li * sx + (long long)gv[m]) : Real(0);
+                }
+#pragma unroll
+                for (int li = 0; li < BX; li++) {
+                    if (li >= ex) break;
+#pragma unroll
+                    for (int m = 0; m < TV; m++)
+                        if (ok[m]) slice2[(lj * BX + li) * CS + t + m * NT] = v[li][m];
+                }
+            }
         }
     }
 
@@ -464,6 +538,28 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
 #pragma unroll
             for (int m = 0; m < TV; m++)
                 if (ok[m]) slice[SL(li, -1) + t + m * NT] = phy[li][m];
+        }
+        if constexpr (ORDER == 2) {
+            // the second halo column / row (read only by cells with both
+            // upwind neighbours in the domain, so not in a first block)
+            if (!xfirst) {
+#pragma unroll
+                for (int lj = 0; lj < BY; lj++) {
+                    if (lj >= ey) break;
+#pragma unroll
+                    for (int m = 0; m < TV; m++)
+                        if (ok[m]) slice[SL(-2, lj) + t + m * NT] = phx2[lj][m];
+                }
+            }
+            if (!yfirst) {
+#pragma unroll
+                for (int li = 0; li < BX; li++) {
+                    if (li >= ex) break;
+#pragma unroll
+                    for (int m = 0; m < TV; m++)
+                        if (ok[m]) slice[SL(li, -2) + t + m * NT] = phy2[li][m];
+                }
+            }
         }
         __syncthreads();
         // c_x = xi_x - U_x of each cell of the slice as a float pair, per x node
@@ -527,7 +623,92 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 return implicit_div(src + ax * fx + ay * fy + az * fz, den);
             }
         };
-        if (ex == BX && ey == BY && !any_solid) {
+        // Order 2: the three-point backward difference along an axis is
+        //   a (3 f - 4 f_1 + f_2) / 2 = (3a/2) (f - h),  h = f_1 + (f_1 - f_2)/3,
+        // so the update is that of Eq. (7) with the coefficient 3a/2 and the
+        // extrapolated upwind value h on the axes where it applies (o2d).
+        auto cell_update2 = [&](const Quad<Real> &c0, const Quad<Real> &c1, const Quad<Real> &c2v,
+                                const Quad<Real> &c3, int m, Real hx, Real hy, Real hz, bool o2x, bool o2y,
+                                bool o2z) -> Real {
+            const Real m2ux = c0.x, m2uy = c0.y, m2uz = c0.z, kappa = c0.w;
+            const Real nexp = c1.x, rt1 = c1.y, rtau = c1.z;
+            const Real qx = c2v.x, qy = c2v.y, qz = c2v.z;
+            const Real shk0 = c3.z, muq = c3.w;
+            const Real cq = fma(xi[m][0], qx, fma(xi[m][1], qy, fma(xi[m][2], qz, muq)));
+            // FP32: the source rtau (f^S - M_ref) of the deviation, evaluated as
+            // rtau M_ref (2^D shak - 1) with D = log2(f^S_M / M_ref) built from
+            // per-cell terms that are small near the reference state, so that
+            // its rounding scales with the deviation rather than with f
+            // (the reference M_ref is the rest state; its own FP32 rounding
+            // error dmref is added back).  FP64: rtau f^S as in Eq. (7).
+            Real dsrc;
+            if constexpr (sizeof(Real) == 4) {
+                const Real dn = c2v.w, K = c3.x;
+                const Real sd = fma(xi[m][0], m2ux, fma(xi[m][1], m2uy, xi[m][2] * m2uz));  // -2 U.xi
+                const Real D = fma(xsq[m], dn, fma(sd, nexp, K));
+                const Real shm1 = cq * fma(xsq[m] + sd, rt1, shk0);  // Shakhov factor - 1
+                const Real em = exp2m1(D);
+                const Real X = fma(em, shm1, em + shm1);  // 2^D shak - 1
+                dsrc = rtau * fma(mref[m], X, dmref[m]);
+                (void)kappa;
+            } else {
+                const Real s = fma(xi[m][0], m2ux, fma(xi[m][1], m2uy, fma(xi[m][2], m2uz, xsq[m])));
+                const Real shak = fma(cq, fma(s, rt1, shk0), Real(1));
+                dsrc = kappa * eq_exp(s * nexp) * shak;
+            }
+            // uniform grids only: a_d per velocity
+            const Real ax = o2x ? Real(1.5) * adx[m][0] : adx[m][0];
+            const Real ay = o2y ? Real(1.5) * adx[m][1] : adx[m][1];
+            const Real az = o2z ? Real(1.5) * adx[m][2] : adx[m][2];
+            const Real den = rtau + ax + ay + az;
+            if constexpr (sizeof(Real) == 4) {
+                // about the upwind x value, as the first-order FP32 update
+                Real t = fma(-rtau, hx, dsrc);
+                t = fma(ay, hy - hx, t);
+                t = fma(az, hz - hx, t);
+                return fma(t, rcp_approx(den), hx);
+            } else {
+                return implicit_div(dsrc + ax * hx + ay * hy + az * hz, den);
+            }
+        };
+        if constexpr (ORDER == 2) {
+            // Generic diagonal loop with the second-order stencil.  The z
+            // values of (i, j) are slice k-1 (in place) and k-2 (slice2);
+            // once the cell is updated, its k-1 value moves to slice2.
+            const int szk = sz0 + lk;
+            const bool o2z = szk >= 2;
+            const Real third = Real(1) / Real(3);
+            for (int d = 0; d < ex + ey - 1; d++) {
+                const int jhi = min(ey - 1, d), jlo = max(0, d - (ex - 1));
+#pragma unroll
+                for (int k = 0; k < BY; k++) {
+                    const int lj = jhi - k;
+                    if (lj >= jlo) {
+                        const int li = d - lj;
+                        const Real *c = cs + (lj * BX + li) * NCOEF;
+                        const Quad<Real> c0 = load_quad(c), c1 = load_quad(c + 4), c2v = load_quad(c + 8),
+                                         c3 = load_quad(c + 12);
+                        const bool o2x = sx0 + li >= 2, o2y = sy0 + lj >= 2;
+                        const int sidx = SL(li, lj), bidx = (lj * BX + li) * CS;
+#pragma unroll
+                        for (int m = 0; m < TV; m++) {
+                            const int vl = t + m * NT;
+                            const Real fz = slice[sidx + vl];
+                            const Real fy = slice[sidx - PX * CS + vl];
+                            const Real fx = slice[sidx - CS + vl];
+                            const Real hx = o2x ? fma(fx - slice[sidx - 2 * CS + vl], third, fx) : fx;
+                            const Real hy = o2y ? fma(fy - slice[sidx - 2 * PX * CS + vl], third, fy) : fy;
+                            const Real hz = o2z ? fma(fz - slice2[bidx + vl], third, fz) : fz;
+                            const Real f = cell_update2(c0, c1, c2v, c3, m, hx, hy, hz, o2x, o2y, o2z);
+                            if (ok[m]) {
+                                slice2[bidx + vl] = fz;
+                                slice[sidx + vl] = f;
+                            }
+                        }
+                    }
+                }
+            }
+        } else if (ex == BX && ey == BY && !any_solid) {
             // Full block without solid cells: the 15 diagonals unrolled.  The
             // upwind x and y values of a cell were computed on the previous
             // diagonal by this thread and stay in registers (prev[row]); only
@@ -553,7 +734,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                             const int vl = t + m * NT;
                             const Real fz = slice[sidx + vl];
                             const Real fx = li == 0 ? slice[sidx - CS + vl] : prev[lj][m];
-                            const Real fy = lj == 0 ? slice[sidx - (BX + 1) * CS + vl] : prev[lj > 0 ? lj - 1 : 0][m];
+                            const Real fy = lj == 0 ? slice[sidx - PX * CS + vl] : prev[lj > 0 ? lj - 1 : 0][m];
                             const Real f = cell_update(c0, c1, c2v, c3, m, fx, fy, fz);
                             prev[lj][m] = f;
                             if (ok[m]) slice[sidx + vl] = f;
@@ -594,7 +775,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                         for (int m = 0; m < TV; m++) {
                             const int vl = t + m * NT;
                             Real fz = slice[sidx + vl];
-                            Real fy = slice[sidx - (BX + 1) * CS + vl];
+                            Real fy = slice[sidx - PX * CS + vl];
                             Real fx = slice[sidx - CS + vl];
                             if (any_solid) {
                                 if (sol_x) fx = ghost(rwx, msol[m], m);
@@ -622,6 +803,18 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
                 for (int m = 0; m < TV; m++)
                     if (ok[m]) fo[lj * step + (long long)gv[m]] = src[m * NT];
             }
+            if constexpr (ORDER == 2) {
+                // the column before the last: the halo column when ex == 1
+                Real *fo2 = FX2p + ((size_t)z * ny + GY(0)) * Nv;
+#pragma unroll
+                for (int lj = 0; lj < BY; lj++) {
+                    if (lj >= ey) break;
+                    const Real *src = slice + SL(ex - 2, lj) + t;
+#pragma unroll
+                    for (int m = 0; m < TV; m++)
+                        if (ok[m]) fo2[lj * step + (long long)gv[m]] = src[m * NT];
+                }
+            }
         }
         if (!ylast) {
             Real *fo = FYp + ((size_t)z * nx + GX(0)) * Nv;
@@ -633,6 +826,17 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
 #pragma unroll
                 for (int m = 0; m < TV; m++)
                     if (ok[m]) fo[li * step + (long long)gv[m]] = src[m * NT];
+            }
+            if constexpr (ORDER == 2) {
+                Real *fo2 = FY2p + ((size_t)z * nx + GX(0)) * Nv;
+#pragma unroll
+                for (int li = 0; li < BX; li++) {
+                    if (li >= ex) break;
+                    const Real *src = slice + SL(li, ey - 2) + t;
+#pragma unroll
+                    for (int m = 0; m < TV; m++)
+                        if (ok[m]) fo2[li * step + (long long)gv[m]] = src[m * NT];
+                }
             }
         }
         __syncthreads();
@@ -871,6 +1075,8 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
             for (int m = 0; m < TV; m++) {
                 if (!ok[m]) continue;
                 FZp[((size_t)y * nx + x) * Nv + gv[m]] = slice[SL(li, lj) + t + m * NT];
+                if constexpr (ORDER == 2)  // slice ez-2 (the inflow slice k0-1 when ez == 1)
+                    FZ2p[((size_t)y * nx + x) * Nv + gv[m]] = slice2[(lj * BX + li) * CS + t + m * NT];
             }
         }
     }
@@ -1077,7 +1283,7 @@ __device__ void chain_add(const SweepArgs &a, int o, int bxr, int byr, int bzr, 
 // and its accumulator-chain predecessor were claimed earlier by CTAs that are
 // running: the waits always end unless an error stopped a producer, and then
 // they end at the poll limit.
-template <typename Real, int TV, int LINE, bool UNIF>
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
 __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSweepArgs b)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1112,7 +1318,7 @@ __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSwee
         __syncthreads();
         if (!s_go) break;
         void *scratch = static_cast<unsigned char *>(b.scratch) + (size_t)blockIdx.x * b.scratch_stride;
-        sweep_item<Real, TV, LINE, true, UNIF>(sa, make_int4(o, bxr, byr, bzr), vg, smem, scratch);
+        sweep_item<Real, TV, LINE, true, UNIF, ORDER>(sa, make_int4(o, bxr, byr, bzr), vg, smem, scratch);
         __syncthreads();
         // the downwind blocks may start: the face planes are written
         if (threadIdx.x == 0 && it != b.skip_publish) {
@@ -1185,42 +1391,42 @@ cudaError_t launch_line(const SweepArgs &a, int n_items, int max_vg, cudaStream_
                      : launch_t<Real, TV, 0, false>(a, n_items, max_vg, s);
 }
 
-template <typename Real, int TV, int LINE, bool UNIF>
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
 cudaError_t launch_persistent_t(const BatchSweepArgs &b, int nxo_max, int grid, cudaStream_t s)
 {
-    using L = SmemLayout<Real, TV>;
+    using L = SmemLayout<Real, TV, ORDER>;
     const size_t bytes = L::total(nxo_max, LINE > 0);
-    cudaError_t e =
-        ensure_smem(reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF>), bytes);
+    const void *fn = reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER>);
+    cudaError_t e = ensure_smem(fn, bytes);
     if (e != cudaSuccess) return e;
-    sweep_persistent_kernel<Real, TV, LINE, UNIF><<<grid, NT, bytes, s>>>(b);
+    sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER><<<grid, NT, bytes, s>>>(b);
     return cudaGetLastError();
 }
 
-template <typename Real, int TV, int LINE, bool UNIF>
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
 int occupancy_t(size_t smem)
 {
     int n = 0;
-    if (ensure_smem(reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF>), smem) !=
-        cudaSuccess) {
+    const void *fn = reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER>);
+    if (ensure_smem(fn, smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_persistent_kernel<Real, TV, LINE, UNIF>, NT, smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER>, NT,
+                                                      smem) != cudaSuccess)
         return 0;
     return n;
 }
 
 // Instantiation for (precision, velocities per thread, line specialisation,
-// uniform grid) chosen at run time.
-template <template <typename, int, int, bool> class F, typename... Args>
+// uniform grid) chosen at run time, first-order sweep.
+template <template <typename, int, int, bool, int> class F, typename... Args>
 auto dispatch(int precision, int tv, int line16, int uniform, Args &&...args)
 {
-#define KGS_CASES(R, T)                                                                \
-    if (line16)                                                                        \
-        return uniform ? F<R, T, 16, true>::run(args...) : F<R, T, 16, false>::run(args...); \
-    return uniform ? F<R, T, 0, true>::run(args...) : F<R, T, 0, false>::run(args...);
+#define KGS_CASES(R, T)                                                                             \
+    if (line16)                                                                                     \
+        return uniform ? F<R, T, 16, true, 1>::run(args...) : F<R, T, 16, false, 1>::run(args...); \
+    return uniform ? F<R, T, 0, true, 1>::run(args...) : F<R, T, 0, false, 1>::run(args...);
     if (precision == 0) {
         KGS_CASES(double, 1)
     }
@@ -1231,36 +1437,52 @@ auto dispatch(int precision, int tv, int line16, int uniform, Args &&...args)
 #undef KGS_CASES
 }
 
-template <typename Real, int TV, int LINE, bool UNIF>
+// The second-order sweep: one velocity per thread, uniform grids.
+template <template <typename, int, int, bool, int> class F, typename... Args>
+auto dispatch_order2(int precision, int line16, Args &&...args)
+{
+    if (precision == 0) return line16 ? F<double, 1, 16, true, 2>::run(args...) : F<double, 1, 0, true, 2>::run(args...);
+    return line16 ? F<float, 1, 16, true, 2>::run(args...) : F<float, 1, 0, true, 2>::run(args...);
+}
+
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
 struct PersistentLaunch {
     static cudaError_t run(const BatchSweepArgs &b, int nxo_max, int grid, cudaStream_t s)
     {
-        return launch_persistent_t<Real, TV, LINE, UNIF>(b, nxo_max, grid, s);
+        return launch_persistent_t<Real, TV, LINE, UNIF, ORDER>(b, nxo_max, grid, s);
     }
 };
 
-template <typename Real, int TV, int LINE, bool UNIF>
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
 struct Occupancy {
-    static int run(size_t smem) { return occupancy_t<Real, TV, LINE, UNIF>(smem); }
+    static int run(size_t smem) { return occupancy_t<Real, TV, LINE, UNIF, ORDER>(smem); }
 };
 
 }  // namespace
 
-int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem)
+int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem, int order)
 {
+    if (order == 2) return (tv == 1 && uniform) ? dispatch_order2<Occupancy>(precision, line16, smem) : 0;
     return dispatch<Occupancy>(precision, tv, line16, uniform, smem);
 }
 
 cudaError_t launch_sweep_persistent(int precision, int tv, int line16, int uniform, const BatchSweepArgs &b,
-                                    int nxo_max, int grid, cudaStream_t s)
+                                    int nxo_max, int grid, cudaStream_t s, int order)
 {
     if (b.n_items == 0) return cudaSuccess;
+    if (order == 2) {
+        if (tv != 1 || !uniform) return cudaErrorInvalidValue;
+        return dispatch_order2<PersistentLaunch>(precision, line16, b, nxo_max, grid, s);
+    }
     return dispatch<PersistentLaunch>(precision, tv, line16, uniform, b, nxo_max, grid, s);
 }
 
-size_t sweep_smem_bytes(int precision, int tv, int line16, int nxo_max)
+size_t sweep_smem_bytes(int precision, int tv, int line16, int nxo_max, int order)
 {
     const bool line = line16 != 0;
+    if (order == 2)
+        return precision == 0 ? SmemLayout<double, 1, 2>::total(nxo_max, line)
+                              : SmemLayout<float, 1, 2>::total(nxo_max, line);
     if (precision == 0) return SmemLayout<double, 1>::total(nxo_max, line);
     return tv == 2 ? SmemLayout<float, 2>::total(nxo_max, line) : SmemLayout<float, 1>::total(nxo_max, line);
 }

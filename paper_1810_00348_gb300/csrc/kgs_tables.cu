@@ -19,7 +19,7 @@ double maxwellian(double rho, const double U[3], double T, const double xi[3])
 
 int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
                      const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z, int vz_begin,
-                     int vz_end)
+                     int vz_end, int order)
 {
     if (!grid || !vg || !gas || !bc) return KGS_EINVAL;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !grid->dx || !grid->dy || !grid->dz) return KGS_EINVAL;
@@ -52,6 +52,20 @@ int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid
     if (solid)
         for (long long i = 0; i < ncell; i++) any_solid |= solid[i] != 0;
     if (any_solid && !(bc->T_solid > 0.0)) return KGS_EINVAL;
+    if (order < 0 || order > 2) return KGS_EINVAL;
+    if (order == 2) {
+        // the three-point difference assumes equal widths along each axis;
+        // the kernel's second-order variant has no solid-cell path and keeps
+        // two slices of 128 velocities in shared memory;
+        // reference state at rest: no free-stream sides (the FP32 form's
+        // deviation source is written about rho = 1, U = 0, T = 1)
+        if (any_solid || any_inflow || v_per_cta == 256) return KGS_EINVAL;
+        const double *w[3] = {grid->dx, grid->dy, grid->dz};
+        const int n[3] = {grid->nx, grid->ny, grid->nz};
+        for (int d = 0; d < 3; d++)
+            for (int i = 1; i < n[d]; i++)
+                if (w[d][i] != w[d][0]) return KGS_EINVAL;
+    }
     if (std::isinf(gas->Kn)) {
         // free-molecular limit: a velocity with all components zero has no
         // equation (0 = 0); such grids are rejected
@@ -66,7 +80,7 @@ int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid
 
 void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg,
                   const kgs_gas *gas, const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z,
-                  int vz_begin, int vz_end)
+                  int vz_begin, int vz_end, int order)
 {
     t.nx = grid->nx;
     t.ny = grid->ny;
@@ -82,7 +96,8 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
     t.wall_norm_mode = wall_norm;
     // defaults measured on the 64^3 x 32^3 cavity: two velocities per thread
     // and 32-cell-deep blocks for the FP32 sweep
-    t.tv = (precision == KGS_FP64) ? 1 : (v_per_cta == 128 ? 1 : 2);
+    t.order = order == 2 ? 2 : 1;
+    t.tv = (precision == KGS_FP64 || t.order == 2) ? 1 : (v_per_cta == 128 ? 1 : 2);
     t.vg_size = NT * t.tv;
     t.bz = block_z > 0 ? block_z : 32;
     t.omega = gas->omega;
@@ -113,18 +128,18 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
     for (int i = 0; i < nz; i++) t.rdz[i] = 1.0 / t.dz[i];
 
     // ---- velocities sorted by octant (bit d set: xi_d >= 0), ix fastest ----
-    std::vector<int> order;
-    order.reserve(t.Nv);
+    std::vector<int> vsorted;
+    vsorted.reserve(t.Nv);
     auto oct_of = [&](int ix, int iy, int iz) {
         return (vg->xi_x[ix] >= 0.0 ? 1 : 0) | (vg->xi_y[iy] >= 0.0 ? 2 : 0) | (vg->xi_z[iz] >= 0.0 ? 4 : 0);
     };
     for (int o = 0; o < 8; o++) {
-        t.oct_vstart[o] = (int)order.size();
+        t.oct_vstart[o] = (int)vsorted.size();
         for (int iz = t.vz0; iz < t.vz1; iz++)
             for (int iy = 0; iy < t.nvy; iy++)
                 for (int ix = 0; ix < t.nvx; ix++)
-                    if (oct_of(ix, iy, iz) == o) order.push_back(ix + t.nvx * (iy + t.nvy * iz));
-        t.oct_vcount[o] = (int)order.size() - t.oct_vstart[o];
+                    if (oct_of(ix, iy, iz) == o) vsorted.push_back(ix + t.nvx * (iy + t.nvy * iz));
+        t.oct_vcount[o] = (int)vsorted.size() - t.oct_vstart[o];
         int cnt = 0;
         for (int ix = 0; ix < t.nvx; ix++) cnt += ((vg->xi_x[ix] >= 0.0 ? 1 : 0) == (o & 1));
         t.oct_nx[o] = cnt;
@@ -141,7 +156,7 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
     t.velm64.assign((size_t)t.Nv * 8, 0.0);
     t.velm32.assign((size_t)t.Nv * 8, 0.f);
     for (int g = 0; g < t.Nv; g++) {
-        const int a = order[g];
+        const int a = vsorted[g];
         const int ix = a % t.nvx, iy = (a / t.nvx) % t.nvy, iz = a / (t.nvx * t.nvy);
         t.vel64[g * 4 + 0] = vg->xi_x[ix];
         t.vel64[g * 4 + 1] = vg->xi_y[iy];
@@ -219,8 +234,10 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
         }
         for (int g = 0; g < t.Nv; g++) {
             const double *v = &t.vel64[g * 4];
-            const float m32 = (float)maxwellian(refRho, refU, refT, v);
+            const double m64 = maxwellian(refRho, refU, refT, v);
+            const float m32 = (float)m64;
             t.velm32[g * 8 + 5] = m32;
+            t.velm32[g * 8 + 6] = (float)(m64 - (double)m32);  // its rounding error (second-order sweep)
             const double wm = v[3] * (double)m32;
             for (int a = 0; a <= 3; a++)
                 for (int b = 0; a + b <= 3; b++)

@@ -16,6 +16,7 @@ constexpr double R_GAS = 0.5;  // velocity unit sqrt(2 R T0)
 struct HostTables {
     int nx = 0, ny = 0, nz = 0, nvx = 0, nvy = 0, nvz = 0, Nv = 0;  // Nv: velocities swept by this context
     int vz0 = 0, vz1 = 0;                    // swept velocity planes iz in [vz0, vz1)
+    int order = 1;                           // upwind order of the sweep (1 or 2)
     size_t ncell = 0;
     long long n_fluid = 0;
     int precision = KGS_FP64, wall_norm_mode = KGS_WALL_DISCRETE;
@@ -65,14 +66,16 @@ struct HostTables {
 
 // Argument checks of kgs_setup (KGS_OK or KGS_EINVAL).
 // vz_begin, vz_end: the velocity planes iz in [vz_begin, vz_end) of a
-// velocity-space partition (0, 0: all of them).
+// velocity-space partition (0, 0: all of them).  order: upwind order of the
+// sweep (0 or 1: Eq. (7); 2: three-point differences, which need equal widths
+// along each axis, no solid cells and 128 velocities per thread block).
 int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
                      const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z, int vz_begin = 0,
-                     int vz_end = 0);
+                     int vz_end = 0, int order = 1);
 
 // Build every host table of a validated problem.
 void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg,
                   const kgs_gas *gas, const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z,
-                  int vz_begin = 0, int vz_end = 0);
+                  int vz_begin = 0, int vz_end = 0, int order = 1);
 
 }  // namespace kgs

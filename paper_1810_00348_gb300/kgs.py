@@ -57,7 +57,7 @@ class KgsOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("wall_norm", ctypes.c_int), ("mass_rescale", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("tol", ctypes.c_double), ("v_per_cta", ctypes.c_int),
                 ("block_z", ctypes.c_int), ("stream", ctypes.c_void_p), ("q_lagged", ctypes.c_int),
-                ("vz_begin", ctypes.c_int), ("vz_end", ctypes.c_int)]
+                ("vz_begin", ctypes.c_int), ("vz_end", ctypes.c_int), ("order", ctypes.c_int)]
 
 
 class KgsInfo(ctypes.Structure):
@@ -187,7 +187,7 @@ def kgs_setup(prob, precision=KGS_FP64, max_iters=1000, tol=1e-8, v_per_cta=0, b
     g, v, gas, bc, solid_p = _problem_structs(prob, keep)
     opts = KgsOpts(precision, int(prob.wall_mode), int(prob.mass_rescale), max_iters, tol, v_per_cta, block_z,
                    ctypes.c_void_p(stream) if stream else None, int(getattr(prob, "q_lagged", 0)),
-                   int(vz[0]), int(vz[1]))
+                   int(vz[0]), int(vz[1]), int(getattr(prob, "order", 1)))
     h = ctypes.c_void_p()
     _check(lib.kgs_setup(ctypes.byref(h), ctypes.byref(g), solid_p, ctypes.byref(v), ctypes.byref(gas),
                          ctypes.byref(bc), ctypes.byref(opts)), "kgs_setup")
