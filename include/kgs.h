@@ -135,7 +135,18 @@ typedef struct {
  *                needs equal cell widths along each axis, no solid cells and
  *                no free-stream sides, holds two slices and two face planes
  *                per direction, and sweeps 128 velocities per thread block
- *                (KGS_EINVAL otherwise). */
+ *                (KGS_EINVAL otherwise).
+ *   dev_source   KGS_MIXED, order 1: 1 evaluates the FP32 sweep's source
+ *                rtau (f^S - M_ref) from the small per-cell differences of the
+ *                exponents of f^S and of the reference Maxwellian at rest
+ *                (a 2^x - 1 series near the reference state), so that its
+ *                rounding scales with the deviation from M_ref rather than
+ *                with f: about 5 times lower residual floor of the mixed
+ *                iteration, at about 1.2 times the sweep time.  Needs equal
+ *                cell widths along each axis and no free-stream sides
+ *                (KGS_EINVAL otherwise).  The order-2 FP32 sweep always uses
+ *                this form; kgs_solve and kgs_batch_solve use it in their
+ *                mixed phase wherever it applies. */
 typedef struct {
     int precision;
     int wall_norm;
@@ -148,6 +159,7 @@ typedef struct {
     int q_lagged;
     int vz_begin, vz_end;
     int order;
+    int dev_source;
 } kgs_opts;
 
 /* Sizes and counters of a context. */

@@ -27,6 +27,7 @@ struct kgs_batch {
     int n = 0;
     std::vector<kgs_ctx *> ctx;
     int precision = KGS_MIXED, tv = 2, bz = 32, line16 = 0, uniform = 0, nxo_max = 1;
+    int dev_src = 0;  // deviation-form FP32 source (kgs_opts.dev_source)
     int max_iters = 1000;
     double tol = 1e-8;
     std::vector<char> active;
@@ -153,7 +154,8 @@ int enqueue_iteration(kgs_batch *b, int which)
     ba.skip_publish = b->skip_publish;
     // external records: inside a capture a plain record only orders streams
     KGS_CHECK(cudaEventRecordWithFlags(b->ev[0], st, cudaEventRecordExternal));
-    KGS_CHECK(launch_sweep_persistent(b->precision, b->tv, b->line16, b->uniform, ba, b->nxo_max, b->grid, st));
+    KGS_CHECK(launch_sweep_persistent(b->precision, b->tv, b->line16, b->uniform, ba, b->nxo_max, b->grid, st, 1,
+                                      b->dev_src));
     KGS_CHECK(cudaEventRecordWithFlags(b->ev[1], st, cudaEventRecordExternal));
     for (int i = 0; i < b->n; i++)
         if (b->active[i] &&
@@ -290,7 +292,8 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     }
     for (int i = 0; i < n; i++) {
         const kgs_problem &p = probs[i];
-        int rc = validate_problem(&p.grid, p.solid, &p.vgrid, &p.gas, &p.bc, opts->precision, p.wall_norm, vpc, bz);
+        int rc = validate_problem(&p.grid, p.solid, &p.vgrid, &p.gas, &p.bc, opts->precision, p.wall_norm, vpc, bz,
+                                  0, 0, 1, opts->dev_source);
         if (rc) return rc;
     }
     (void)cudaGetLastError();  // launches below check their own status
@@ -309,6 +312,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     }
     b->n = n;
     b->precision = opts->precision;
+    b->dev_src = opts->dev_source ? 1 : 0;
     b->max_iters = opts->max_iters > 0 ? opts->max_iters : 1000;
     b->tol = opts->tol > 0.0 ? opts->tol : 1e-8;
     b->ctx.assign(n, nullptr);
@@ -325,6 +329,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
         o.mass_rescale = p.mass_rescale;
         o.q_lagged = p.q_lagged;
         o.order = 1;
+        o.dev_source = opts->dev_source;
         o.v_per_cta = vpc;
         o.block_z = bz;
         int rc = ctx_create(&b->ctx[i], &p.grid, p.solid, &p.vgrid, &p.gas, &p.bc, &o);
@@ -362,7 +367,7 @@ int kgs_batch_setup(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess) return fail(KGS_ECUDA);
     const size_t smem = sweep_smem_bytes(b->precision, b->tv, b->line16, b->nxo_max);
-    per_sm = sweep_persistent_occupancy(b->precision, b->tv, b->line16, b->uniform, smem);
+    per_sm = sweep_persistent_occupancy(b->precision, b->tv, b->line16, b->uniform, smem, 1, b->dev_src);
     if (per_sm < 1) return fail(KGS_ECUDA);
     b->grid = sms * per_sm;
     b->scratch_stride = sweep_scratch_bytes(b->bz);
@@ -422,6 +427,10 @@ int kgs_batch_solve(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     // progress (the rule of kgs_solve, per instance), then retires
     kgs_opts om = *opts;
     om.precision = KGS_MIXED;
+    // the deviation-form source (lower residual floor) where every instance allows it
+    om.dev_source = 1;
+    for (int i = 0; i < n; i++)
+        if (!dev_source_applies(&probs[i].grid, &probs[i].bc)) om.dev_source = 0;
     int rc = kgs_batch_setup(&m, n, probs, &om);
     if (rc) return finish(rc);
     if (cudaSetDevice(m->dev) != cudaSuccess) return finish(KGS_ECUDA);
@@ -456,6 +465,7 @@ int kgs_batch_solve(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     // FP64 phase from each mixed state (macros, wall densities, mass target)
     kgs_opts od = *opts;
     od.precision = KGS_FP64;
+    od.dev_source = 0;
     od.v_per_cta = 128;
     od.block_z = opts->block_z > 0 ? opts->block_z : 32;
     if ((rc = kgs_batch_setup(&d, n, probs, &od))) return finish(rc);

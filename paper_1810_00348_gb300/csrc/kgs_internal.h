@@ -182,11 +182,13 @@ __device__ __forceinline__ int flag_bits(float v) { return __float_as_int(v); }
 __device__ __forceinline__ int flag_bits(double v) { return (int)__double_as_longlong(v); }
 
 // order: upwind order of the sweep; order 2 exists for tv = 1 on uniform
-// grids only (0 CTAs per SM / cudaErrorInvalidValue otherwise).
+// grids only.  dev: the first-order FP32 sweep with the deviation-form source
+// (uniform grids).  Other combinations: 0 CTAs per SM / cudaErrorInvalidValue.
 cudaError_t launch_sweep_persistent(int precision, int tv, int line16, int uniform, const BatchSweepArgs &b, int nxo_max,
-                                    int grid, cudaStream_t s, int order = 1);
+                                    int grid, cudaStream_t s, int order = 1, int dev = 0);
 // Resident CTAs per SM of the persistent kernel (also sets its shared-memory limit).
-int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem, int order = 1);
+int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem, int order = 1,
+                               int dev = 0);
 
 // Sweep launch (one wavefront stage, order 1).  precision: 0 FP64, 1 FP32.
 cudaError_t launch_sweep(int precision, int tv, const SweepArgs &a, int n_items, int max_vg, cudaStream_t s);

@@ -188,7 +188,7 @@ int kgs::ctx_launch_coef(kgs_ctx *c)
 {
     const HostTables &t = c->t;
     KGS_CHECK(launch_coef(t.precision, c->mac, c->solid, c->side_flags, c->rdx, c->rdy, c->rdz, t.nx, t.ny, t.nz,
-                          t.mu_ref, t.omega, t.Pr, c->coef, c->stream, t.order == 2 && t.precision == KGS_MIXED));
+                          t.mu_ref, t.omega, t.Pr, c->coef, c->stream, t.dev ? 1 : 0));
     c->kernel_launches += 1;
     return KGS_OK;
 }
@@ -222,7 +222,7 @@ int kgs::ctx_launch_stages(kgs_ctx *c)
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[0], st));
         KGS_CHECK(
             launch_sweep_persistent(t.precision, t.tv, a.line16, a.uniform, ba, t.nxo_max, c->persist_grid, st,
-                                    t.order));
+                                    t.order, t.dev && t.order == 1));
         if (c->profiling) KGS_CHECK(cudaEventRecord(c->ev[1], st));
         c->kernel_launches += 1;
         c->sweep_launches += 1;
@@ -295,9 +295,10 @@ int kgs::ctx_persist_init(kgs_ctx *c)
     const SweepArgs a = ctx_sweep_args(c);
     const int per_sm = sweep_persistent_occupancy(t.precision, t.tv, a.line16, a.uniform,
                                                   sweep_smem_bytes(t.precision, t.tv, a.line16, t.nxo_max, t.order),
-                                                  t.order);
-    // the second-order sweep exists only as the persistent kernel
-    if (per_sm < 1 && t.order == 2) return KGS_EINVAL;
+                                                  t.order, t.dev && t.order == 1);
+    // the second-order sweep and the deviation-form source exist only in the
+    // persistent kernel
+    if (per_sm < 1 && (t.order == 2 || t.dev)) return KGS_EINVAL;
     if (per_sm < 1) {
         // the launch per stage, with per-group partials
         return dalloc(c, &c->part, (size_t)t.n_vg * NPART * t.ncell * 8);
@@ -451,7 +452,7 @@ int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const k
     if (!out || !opts) return KGS_EINVAL;
     *out = nullptr;
     int rc = validate_problem(grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta,
-                              opts->block_z, opts->vz_begin, opts->vz_end, opts->order);
+                              opts->block_z, opts->vz_begin, opts->vz_end, opts->order, opts->dev_source);
     if (rc) return rc;
     (void)cudaGetLastError();  // launches below check their own status
     if ((rc = ctx_create(out, grid, solid, vg, gas, bc, opts))) return rc;
@@ -484,7 +485,7 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
     c->tol = opts->tol > 0.0 ? opts->tol : 1e-8;
     HostTables &t = c->t;
     build_tables(t, grid, solid, vg, gas, bc, opts->precision, opts->wall_norm, opts->v_per_cta, opts->block_z,
-                 opts->vz_begin, opts->vz_end, opts->order);
+                 opts->vz_begin, opts->vz_end, opts->order, opts->dev_source);
     c->q_lagged = opts->q_lagged ? 1 : 0;
     const size_t n = t.ncell;
     const size_t rsz = t.real_bytes();

@@ -57,6 +57,8 @@ extern "C" int kgs_solve(const kgs_problem *p, const double *initial, double tol
         return code;
     };
     kgs_opts om = opts_for(p, KGS_MIXED, tol, max_iters, stream);
+    // the deviation-form source lowers the mixed phase's residual floor
+    om.dev_source = kgs::dev_source_applies(&p->grid, &p->bc) ? 1 : 0;
     if ((rc = kgs_setup(&m, &p->grid, p->solid, &p->vgrid, &p->gas, &p->bc, &om))) return finish(rc);
     if (initial && (rc = kgs_set_initial(m, initial))) return finish(rc);
     // mixed phase

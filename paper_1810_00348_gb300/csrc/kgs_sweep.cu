@@ -241,10 +241,13 @@ __device__ __forceinline__ Real ld_face(const Real *p)
 // ORDER 2 (second-order upwind, single contexts on solid-free uniform grids):
 // slice2 keeps slice k-2 at the block's cells, the halo is two cells wide,
 // and FX2/FY2/FZ2 carry the block outflow one cell further upwind.
-template <typename Real, int TV, int LINE, bool COHERENT, bool UNIF, int ORDER = 1>
+template <typename Real, int TV, int LINE, bool COHERENT, bool UNIF, int ORDER = 1, bool DEV = false>
 __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, const int vgy, unsigned char *smem,
                                            void *scratch)
 {
+    // the deviation-form FP32 source (uniform grids: it uses the width slots)
+    constexpr bool DEVF = sizeof(Real) == 4 && (ORDER == 2 || DEV);
+    static_assert(!DEVF || UNIF, "the deviation-form source needs a uniform grid");
     using L = SmemLayout<Real, TV, ORDER>;
     constexpr int VG = L::VG;
     constexpr int CS = L::CS;
@@ -316,7 +319,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
     // the velocity); every ghost value enters as ghost - M_ref and the source
     // as f^S/tau - M_ref/tau.  The FP64 sweep carries f (mref unused).
     Real xi[TV][3], axi[TV][3], mgx[TV], mgy[TV], mgz[TV], msol[TV], mref[TV];
-    Real dmref[ORDER == 2 ? TV : 1];  // order 2, FP32: the rounding error of M_ref
+    Real dmref[TV];  // deviation-form source: the rounding error of M_ref
     size_t gv[TV];
     bool ok[TV];
     const int rowx = a.side_inflow[sidex] ? MT_INFLOW : sidex;
@@ -348,7 +351,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         mgz[m] = mt[(size_t)rowz * Nv + gv[m]];
         msol[m] = mt[(size_t)MT_SOLID * Nv + gv[m]];
         mref[m] = sizeof(Real) == 4 ? velm[gv[m] * 8 + 5] : Real(0);
-        if constexpr (ORDER == 2) dmref[m] = sizeof(Real) == 4 ? velm[gv[m] * 8 + 6] : Real(0);
+        if constexpr (DEVF) dmref[m] = velm[gv[m] * 8 + 6];
     }
     // ghost value rho_w * (unit wall or free-stream Maxwellian), as carried
     auto ghost = [&](Real rw, Real mg, int m) -> Real {
@@ -577,10 +580,37 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
         if (lk + 1 < ez) prefetch(lk + 1);
 
         // ---- sweep of the slice: Eq. (2) fused into Eq. (7), by anti-diagonals ----
+        // FP32 deviation-form source (DEVF: order 2, or the dev_source
+        // option): rtau (f^S - M_ref) evaluated as rtau M_ref (2^D shak - 1)
+        // with D = log2(f^S_M / M_ref) built from per-cell terms that are small
+        // near the reference state (coefficient slots C_RDX, C_RDY of uniform
+        // grids), so that its rounding scales with the deviation g rather than
+        // with f; the reference M_ref is the rest state and its own FP32
+        // rounding error dmref is added back.
+        auto dev_source = [&](const Quad<Real> &c0, const Quad<Real> &c1, const Quad<Real> &c2v,
+                              const Quad<Real> &c3, int m, Real cq) -> Real {
+            const Real dn = c2v.w, K = c3.x;
+            const Real sd = fma(xi[m][0], c0.x, fma(xi[m][1], c0.y, xi[m][2] * c0.z));  // -2 U.xi
+            const Real D = fma(xsq[m], dn, fma(sd, c1.x, K));
+            const Real shm1 = cq * fma(xsq[m] + sd, c1.y, c3.z);  // Shakhov factor - 1
+            const Real em = exp2m1(D);
+            const Real X = fma(em, shm1, em + shm1);  // 2^D shak - 1
+            return c1.z * fma(mref[m], X, dmref[m]);
+        };
         // Eq. (2) fused into Eq. (7) for one cell of the slice (coefficients
         // c0..c3) and thread velocity m, from its three upwind values.
         auto cell_update = [&](const Quad<Real> &c0, const Quad<Real> &c1, const Quad<Real> &c2v,
                                const Quad<Real> &c3, int m, Real fx, Real fy, Real fz) -> Real {
+          if constexpr (DEVF) {
+            // uniform grids only (a_d per velocity); the update about the
+            // upwind x value as below, with the deviation-form source
+            const Real cq = fma(xi[m][0], c2v.x, fma(xi[m][1], c2v.y, fma(xi[m][2], c2v.z, c3.w)));
+            const Real dsrc = dev_source(c0, c1, c2v, c3, m, cq);
+            Real t = fma(-c1.z, fx, dsrc);
+            t = fma(adx[m][1], fy - fx, t);
+            t = fma(adx[m][2], fz - fx, t);
+            return fma(t, rcp_approx(c1.z + asum[m]), fx);
+          } else {
             const Real m2ux = c0.x, m2uy = c0.y, m2uz = c0.z, kappa = c0.w;
             const Real nexp = c1.x, rt1 = c1.y, rtau = c1.z;
             const Real qx = c2v.x, qy = c2v.y, qz = c2v.z, rdx = c2v.w;
@@ -622,6 +652,7 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
             } else {
                 return implicit_div(src + ax * fx + ay * fy + az * fz, den);
             }
+          }
         };
         // Order 2: the three-point backward difference along an axis is
         //   a (3 f - 4 f_1 + f_2) / 2 = (3a/2) (f - h),  h = f_1 + (f_1 - f_2)/3,
@@ -635,21 +666,10 @@ __device__ __forceinline__ void sweep_item(const SweepArgs &a, const int4 w, con
             const Real qx = c2v.x, qy = c2v.y, qz = c2v.z;
             const Real shk0 = c3.z, muq = c3.w;
             const Real cq = fma(xi[m][0], qx, fma(xi[m][1], qy, fma(xi[m][2], qz, muq)));
-            // FP32: the source rtau (f^S - M_ref) of the deviation, evaluated as
-            // rtau M_ref (2^D shak - 1) with D = log2(f^S_M / M_ref) built from
-            // per-cell terms that are small near the reference state, so that
-            // its rounding scales with the deviation rather than with f
-            // (the reference M_ref is the rest state; its own FP32 rounding
-            // error dmref is added back).  FP64: rtau f^S as in Eq. (7).
+            // FP32: the deviation-form source; FP64: rtau f^S as in Eq. (7)
             Real dsrc;
             if constexpr (sizeof(Real) == 4) {
-                const Real dn = c2v.w, K = c3.x;
-                const Real sd = fma(xi[m][0], m2ux, fma(xi[m][1], m2uy, xi[m][2] * m2uz));  // -2 U.xi
-                const Real D = fma(xsq[m], dn, fma(sd, nexp, K));
-                const Real shm1 = cq * fma(xsq[m] + sd, rt1, shk0);  // Shakhov factor - 1
-                const Real em = exp2m1(D);
-                const Real X = fma(em, shm1, em + shm1);  // 2^D shak - 1
-                dsrc = rtau * fma(mref[m], X, dmref[m]);
+                dsrc = dev_source(c0, c1, c2v, c3, m, cq);
                 (void)kappa;
             } else {
                 const Real s = fma(xi[m][0], m2ux, fma(xi[m][1], m2uy, fma(xi[m][2], m2uz, xsq[m])));
@@ -1283,7 +1303,7 @@ __device__ void chain_add(const SweepArgs &a, int o, int bxr, int byr, int bzr, 
 // and its accumulator-chain predecessor were claimed earlier by CTAs that are
 // running: the waits always end unless an error stopped a producer, and then
 // they end at the poll limit.
-template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER, bool DEV>
 __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSweepArgs b)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1318,7 +1338,7 @@ __global__ void __launch_bounds__(NT, 2) sweep_persistent_kernel(const BatchSwee
         __syncthreads();
         if (!s_go) break;
         void *scratch = static_cast<unsigned char *>(b.scratch) + (size_t)blockIdx.x * b.scratch_stride;
-        sweep_item<Real, TV, LINE, true, UNIF, ORDER>(sa, make_int4(o, bxr, byr, bzr), vg, smem, scratch);
+        sweep_item<Real, TV, LINE, true, UNIF, ORDER, DEV>(sa, make_int4(o, bxr, byr, bzr), vg, smem, scratch);
         __syncthreads();
         // the downwind blocks may start: the face planes are written
         if (threadIdx.x == 0 && it != b.skip_publish) {
@@ -1391,42 +1411,42 @@ cudaError_t launch_line(const SweepArgs &a, int n_items, int max_vg, cudaStream_
                      : launch_t<Real, TV, 0, false>(a, n_items, max_vg, s);
 }
 
-template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER, bool DEV>
 cudaError_t launch_persistent_t(const BatchSweepArgs &b, int nxo_max, int grid, cudaStream_t s)
 {
     using L = SmemLayout<Real, TV, ORDER>;
     const size_t bytes = L::total(nxo_max, LINE > 0);
-    const void *fn = reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER>);
+    const void *fn = reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER, DEV>);
     cudaError_t e = ensure_smem(fn, bytes);
     if (e != cudaSuccess) return e;
-    sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER><<<grid, NT, bytes, s>>>(b);
+    sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER, DEV><<<grid, NT, bytes, s>>>(b);
     return cudaGetLastError();
 }
 
-template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER, bool DEV>
 int occupancy_t(size_t smem)
 {
     int n = 0;
-    const void *fn = reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER>);
+    const void *fn = reinterpret_cast<const void *>(sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER, DEV>);
     if (ensure_smem(fn, smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return 0;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER>, NT,
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_persistent_kernel<Real, TV, LINE, UNIF, ORDER, DEV>,
+                                                      NT, smem) != cudaSuccess)
         return 0;
     return n;
 }
 
 // Instantiation for (precision, velocities per thread, line specialisation,
 // uniform grid) chosen at run time, first-order sweep.
-template <template <typename, int, int, bool, int> class F, typename... Args>
+template <template <typename, int, int, bool, int, bool> class F, typename... Args>
 auto dispatch(int precision, int tv, int line16, int uniform, Args &&...args)
 {
-#define KGS_CASES(R, T)                                                                             \
-    if (line16)                                                                                     \
-        return uniform ? F<R, T, 16, true, 1>::run(args...) : F<R, T, 16, false, 1>::run(args...); \
-    return uniform ? F<R, T, 0, true, 1>::run(args...) : F<R, T, 0, false, 1>::run(args...);
+#define KGS_CASES(R, T)                                                                                   \
+    if (line16)                                                                                           \
+        return uniform ? F<R, T, 16, true, 1, false>::run(args...) : F<R, T, 16, false, 1, false>::run(args...); \
+    return uniform ? F<R, T, 0, true, 1, false>::run(args...) : F<R, T, 0, false, 1, false>::run(args...);
     if (precision == 0) {
         KGS_CASES(double, 1)
     }
@@ -1438,41 +1458,56 @@ auto dispatch(int precision, int tv, int line16, int uniform, Args &&...args)
 }
 
 // The second-order sweep: one velocity per thread, uniform grids.
-template <template <typename, int, int, bool, int> class F, typename... Args>
+template <template <typename, int, int, bool, int, bool> class F, typename... Args>
 auto dispatch_order2(int precision, int line16, Args &&...args)
 {
-    if (precision == 0) return line16 ? F<double, 1, 16, true, 2>::run(args...) : F<double, 1, 0, true, 2>::run(args...);
-    return line16 ? F<float, 1, 16, true, 2>::run(args...) : F<float, 1, 0, true, 2>::run(args...);
+    if (precision == 0)
+        return line16 ? F<double, 1, 16, true, 2, false>::run(args...) : F<double, 1, 0, true, 2, false>::run(args...);
+    return line16 ? F<float, 1, 16, true, 2, true>::run(args...) : F<float, 1, 0, true, 2, true>::run(args...);
 }
 
-template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
+// The first-order FP32 sweep with the deviation-form source, uniform grids.
+template <template <typename, int, int, bool, int, bool> class F, typename... Args>
+auto dispatch_dev(int tv, int line16, Args &&...args)
+{
+    if (tv == 2)
+        return line16 ? F<float, 2, 16, true, 1, true>::run(args...) : F<float, 2, 0, true, 1, true>::run(args...);
+    return line16 ? F<float, 1, 16, true, 1, true>::run(args...) : F<float, 1, 0, true, 1, true>::run(args...);
+}
+
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER, bool DEV>
 struct PersistentLaunch {
     static cudaError_t run(const BatchSweepArgs &b, int nxo_max, int grid, cudaStream_t s)
     {
-        return launch_persistent_t<Real, TV, LINE, UNIF, ORDER>(b, nxo_max, grid, s);
+        return launch_persistent_t<Real, TV, LINE, UNIF, ORDER, DEV>(b, nxo_max, grid, s);
     }
 };
 
-template <typename Real, int TV, int LINE, bool UNIF, int ORDER>
+template <typename Real, int TV, int LINE, bool UNIF, int ORDER, bool DEV>
 struct Occupancy {
-    static int run(size_t smem) { return occupancy_t<Real, TV, LINE, UNIF, ORDER>(smem); }
+    static int run(size_t smem) { return occupancy_t<Real, TV, LINE, UNIF, ORDER, DEV>(smem); }
 };
 
 }  // namespace
 
-int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem, int order)
+int sweep_persistent_occupancy(int precision, int tv, int line16, int uniform, size_t smem, int order, int dev)
 {
     if (order == 2) return (tv == 1 && uniform) ? dispatch_order2<Occupancy>(precision, line16, smem) : 0;
+    if (dev) return (precision != 0 && uniform) ? dispatch_dev<Occupancy>(tv, line16, smem) : 0;
     return dispatch<Occupancy>(precision, tv, line16, uniform, smem);
 }
 
 cudaError_t launch_sweep_persistent(int precision, int tv, int line16, int uniform, const BatchSweepArgs &b,
-                                    int nxo_max, int grid, cudaStream_t s, int order)
+                                    int nxo_max, int grid, cudaStream_t s, int order, int dev)
 {
     if (b.n_items == 0) return cudaSuccess;
     if (order == 2) {
         if (tv != 1 || !uniform) return cudaErrorInvalidValue;
         return dispatch_order2<PersistentLaunch>(precision, line16, b, nxo_max, grid, s);
+    }
+    if (dev) {
+        if (precision == 0 || !uniform) return cudaErrorInvalidValue;
+        return dispatch_dev<PersistentLaunch>(tv, line16, b, nxo_max, grid, s);
     }
     return dispatch<PersistentLaunch>(precision, tv, line16, uniform, b, nxo_max, grid, s);
 }

@@ -17,9 +17,21 @@ double maxwellian(double rho, const double U[3], double T, const double xi[3])
 
 }  // namespace
 
+bool dev_source_applies(const kgs_grid *grid, const kgs_bc *bc)
+{
+    for (int s = 0; s < 6; s++)
+        if (bc->type[s] == KGS_FACE_INFLOW) return false;
+    const double *w[3] = {grid->dx, grid->dy, grid->dz};
+    const int n[3] = {grid->nx, grid->ny, grid->nz};
+    for (int d = 0; d < 3; d++)
+        for (int i = 1; i < n[d]; i++)
+            if (w[d][i] != w[d][0]) return false;
+    return true;
+}
+
 int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
                      const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z, int vz_begin,
-                     int vz_end, int order)
+                     int vz_end, int order, int dev_source)
 {
     if (!grid || !vg || !gas || !bc) return KGS_EINVAL;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !grid->dx || !grid->dy || !grid->dz) return KGS_EINVAL;
@@ -52,7 +64,8 @@ int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid
     if (solid)
         for (long long i = 0; i < ncell; i++) any_solid |= solid[i] != 0;
     if (any_solid && !(bc->T_solid > 0.0)) return KGS_EINVAL;
-    if (order < 0 || order > 2) return KGS_EINVAL;
+    if (order < 0 || order > 2 || dev_source < 0 || dev_source > 1) return KGS_EINVAL;
+    if (dev_source && (precision != KGS_MIXED || !dev_source_applies(grid, bc))) return KGS_EINVAL;
     if (order == 2) {
         // the three-point difference assumes equal widths along each axis;
         // the kernel's second-order variant has no solid-cell path and keeps
@@ -80,7 +93,7 @@ int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid
 
 void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg,
                   const kgs_gas *gas, const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z,
-                  int vz_begin, int vz_end, int order)
+                  int vz_begin, int vz_end, int order, int dev_source)
 {
     t.nx = grid->nx;
     t.ny = grid->ny;
@@ -97,6 +110,7 @@ void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, con
     // defaults measured on the 64^3 x 32^3 cavity: two velocities per thread
     // and 32-cell-deep blocks for the FP32 sweep
     t.order = order == 2 ? 2 : 1;
+    t.dev = precision == KGS_MIXED && (t.order == 2 || dev_source != 0);
     t.tv = (precision == KGS_FP64 || t.order == 2) ? 1 : (v_per_cta == 128 ? 1 : 2);
     t.vg_size = NT * t.tv;
     t.bz = block_z > 0 ? block_z : 32;

@@ -17,6 +17,7 @@ struct HostTables {
     int nx = 0, ny = 0, nz = 0, nvx = 0, nvy = 0, nvz = 0, Nv = 0;  // Nv: velocities swept by this context
     int vz0 = 0, vz1 = 0;                    // swept velocity planes iz in [vz0, vz1)
     int order = 1;                           // upwind order of the sweep (1 or 2)
+    bool dev = false;                        // FP32 deviation-form source (order 2, or the option)
     size_t ncell = 0;
     long long n_fluid = 0;
     int precision = KGS_FP64, wall_norm_mode = KGS_WALL_DISCRETE;
@@ -71,11 +72,15 @@ struct HostTables {
 // along each axis, no solid cells and 128 velocities per thread block).
 int validate_problem(const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg, const kgs_gas *gas,
                      const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z, int vz_begin = 0,
-                     int vz_end = 0, int order = 1);
+                     int vz_end = 0, int order = 1, int dev_source = 0);
+
+// The deviation-form FP32 source applies: equal widths along each axis and
+// no free-stream side (the reference Maxwellian is the rest state).
+bool dev_source_applies(const kgs_grid *grid, const kgs_bc *bc);
 
 // Build every host table of a validated problem.
 void build_tables(HostTables &t, const kgs_grid *grid, const uint8_t *solid, const kgs_vgrid *vg,
                   const kgs_gas *gas, const kgs_bc *bc, int precision, int wall_norm, int v_per_cta, int block_z,
-                  int vz_begin = 0, int vz_end = 0, int order = 1);
+                  int vz_begin = 0, int vz_end = 0, int order = 1, int dev_source = 0);
 
 }  // namespace kgs

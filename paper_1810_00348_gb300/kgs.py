@@ -57,7 +57,8 @@ class KgsOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("wall_norm", ctypes.c_int), ("mass_rescale", ctypes.c_int),
                 ("max_iters", ctypes.c_int), ("tol", ctypes.c_double), ("v_per_cta", ctypes.c_int),
                 ("block_z", ctypes.c_int), ("stream", ctypes.c_void_p), ("q_lagged", ctypes.c_int),
-                ("vz_begin", ctypes.c_int), ("vz_end", ctypes.c_int), ("order", ctypes.c_int)]
+                ("vz_begin", ctypes.c_int), ("vz_end", ctypes.c_int), ("order", ctypes.c_int),
+                ("dev_source", ctypes.c_int)]
 
 
 class KgsInfo(ctypes.Structure):
@@ -179,15 +180,16 @@ def _problem_structs(prob, keep):
 
 
 def kgs_setup(prob, precision=KGS_FP64, max_iters=1000, tol=1e-8, v_per_cta=0, block_z=0, stream=None,
-              vz=(0, 0)):
+              vz=(0, 0), dev_source=0):
     """kgs_setup for an ``inputs.Problem``; stream is a cudaStream_t value (int) or None; vz = (begin, end)
-    sweeps only those velocity planes (a part of a velocity-space partition)."""
+    sweeps only those velocity planes (a part of a velocity-space partition); dev_source = 1 selects the
+    deviation-form FP32 source (kgs_opts.dev_source)."""
     lib = load()
     keep = []
     g, v, gas, bc, solid_p = _problem_structs(prob, keep)
     opts = KgsOpts(precision, int(prob.wall_mode), int(prob.mass_rescale), max_iters, tol, v_per_cta, block_z,
                    ctypes.c_void_p(stream) if stream else None, int(getattr(prob, "q_lagged", 0)),
-                   int(vz[0]), int(vz[1]), int(getattr(prob, "order", 1)))
+                   int(vz[0]), int(vz[1]), int(getattr(prob, "order", 1)), int(dev_source))
     h = ctypes.c_void_p()
     _check(lib.kgs_setup(ctypes.byref(h), ctypes.byref(g), solid_p, ctypes.byref(v), ctypes.byref(gas),
                          ctypes.byref(bc), ctypes.byref(opts)), "kgs_setup")
