@@ -226,6 +226,8 @@ def run_ours(args, world, rank, local):
     peaks = _peaks()
     workload = WORKLOAD if (args.cells, args.vels) == (N_CELL, N_VEL) else \
         "3D lid-driven cavity %d^3 cells x %d^3 velocities, Kn=1, lid 0.16" % (args.cells, args.vels)
+    if args.dev_source:
+        workload += ", deviation-form FP32 source"
 
     def barrier():
         if pg is not None:
@@ -249,7 +251,8 @@ def run_ours(args, world, rank, local):
         return ms, sweep_ms, sweep_launches, launches
 
     # ---- mixed precision (headline) ----
-    ctx = kgs.kgs_setup(prob, precision=kgs.KGS_MIXED, v_per_cta=args.v_per_cta, block_z=args.block_z)
+    ctx = kgs.kgs_setup(prob, precision=kgs.KGS_MIXED, v_per_cta=args.v_per_cta, block_z=args.block_z,
+                        dev_source=args.dev_source)
     kgs.kgs_set_profiling(ctx, True)
     info = kgs.kgs_info(ctx)
     kgs.kgs_iterate(ctx, args.warmup)
@@ -338,6 +341,12 @@ def run_ours(args, world, rank, local):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle_sample(kgs)
+        cores = os.cpu_count() or 1
+        if cores > 1:
+            # the same sample on every host core (concurrent velocity ranges)
+            allc = time_oracle_sample(threads=cores)
+            if allc["cores"] > 1:
+                cpu["all_cores"] = {"value": allc["value"], "cores": allc["cores"], "sample": allc["sample"]}
     line = {
         "metric": METRIC, "value": value, "unit": "phase-point updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -711,6 +720,8 @@ def main():
     ap.add_argument("--c5-fp64", type=int, default=1, help="also time the plain FP64 solve from the uniform state")
     ap.add_argument("--cells", type=int, default=N_CELL, help="cells per side (profiling runs only)")
     ap.add_argument("--vels", type=int, default=N_VEL, help="velocities per side (profiling runs only)")
+    ap.add_argument("--dev-source", type=int, default=0,
+                    help="1: the headline leg with the deviation-form FP32 source (profiling runs only)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.only_c5:
