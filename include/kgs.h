@@ -354,9 +354,12 @@ void kgs_batch_destroy(kgs_batch *b);
 /* ---- solve to a tolerance: mixed precision, then FP64 ----
  * The FP32 form of the iteration settles into rounding noise around its
  * fixed point, so its residual stops falling at a floor (about 3e-5 on the
- * cavity's spanwise momentum).  kgs_solve runs mixed iterations in chunks of
- * 5 while the residual keeps falling (below 0.9 x its best value within two
- * chunks once it is below 1e-3, within twenty chunks above), then continues
+ * cavity's spanwise momentum, about 1e-6 with the deviation-form source the
+ * mixed phase uses on wall-bounded uniform grids).  kgs_solve runs mixed
+ * iterations in chunks of 5 while the residual keeps falling (below 0.9 x its
+ * best value within twenty chunks while it is above 1e-3, within six chunks
+ * down to 3e-6, within two chunks below: at small Kn the residual falls with
+ * bumps of about 25 iterations), then continues
  * in FP64 from the mixed state (macros, wall
  * densities and mass target carried over as by kgs_save / kgs_load) until
  * the residual is below tol or max_iters iterations ran in all.

@@ -452,7 +452,7 @@ int kgs_batch_solve(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
             if (!retire) {
                 if (r < SOLVE_PROGRESS * best[i])
                     stalled[i] = 0;
-                else if (++stalled[i] >= (r < SOLVE_NEAR_FLOOR ? SOLVE_PATIENCE : SOLVE_PATIENCE_FAR))
+                else if (++stalled[i] >= solve_patience(r))
                     retire = true;
                 best[i] = std::min(best[i], r);
             }

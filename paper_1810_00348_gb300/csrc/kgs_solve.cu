@@ -5,11 +5,16 @@
 // into a band of rounding noise around its fixed point instead of reaching
 // it; the residual (relative L2 change per iteration, Section 4.1) then stops
 // falling at a floor set by the smallest field (about 3e-5 for the cavity's
-// spanwise momentum).  The FP64 iteration started from that state needs few
-// iterations to reach a tighter tolerance because the state is already within
-// the noise band of the fixed point.  Early in a solve at small Kn the
-// residual can rise for a while before it falls, so the switch waits for a
-// stall only once the residual is below 1e-3 (the floor lies well below).
+// spanwise momentum with the plain FP32 source, about 1e-6 with the
+// deviation-form source).  The FP64 iteration started from that state needs
+// few iterations to reach a tighter tolerance because the state is already
+// within the noise band of the fixed point.  Before the floor, a small-Kn
+// residual does not fall monotonically: it first rises for a while, and
+// later falls with bumps of about 25 iterations, so a stall counts as the
+// floor only after twenty chunks above 1e-3, six chunks down to 3e-6 and two
+// chunks below (kgs::solve_patience).  Leaving the mixed phase at a bump
+// costs the FP64 iterations that the mixed form would have done about twenty
+// times faster.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,10 +25,8 @@
 namespace {
 
 using kgs::SOLVE_CHUNK;
-using kgs::SOLVE_NEAR_FLOOR;
-using kgs::SOLVE_PATIENCE;
-using kgs::SOLVE_PATIENCE_FAR;
 using kgs::SOLVE_PROGRESS;
+using kgs::solve_patience;
 
 kgs_opts opts_for(const kgs_problem *p, int precision, double tol, int max_iters, void *stream)
 {
@@ -72,7 +75,7 @@ extern "C" int kgs_solve(const kgs_problem *p, const double *initial, double tol
         if (r < tol) break;
         if (r < SOLVE_PROGRESS * best) {
             stalled = 0;
-        } else if (++stalled >= (r < SOLVE_NEAR_FLOOR ? SOLVE_PATIENCE : SOLVE_PATIENCE_FAR)) {
+        } else if (++stalled >= solve_patience(r)) {
             break;
         }
         best = std::min(best, r);
