@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libkgs.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["kgs_runtime.cu", "kgs_tables.cu", "kgs_sweep.cu", "kgs_closure.cu", "kgs_noalloc.cu", "kgs_batch.cu", "kgs_autotune.cu", "kgs_nn.cu", "kgs_conv_tc.cu", "kgs_solve.cu"]
-HEADERS = [os.path.join(CSRC, "kgs_internal.h"), os.path.join(CSRC, "kgs_nn.h"), os.path.join(CSRC, "kgs_tables.h"), os.path.join(CSRC, "kgs_ctx.h"), os.path.join(ROOT, "include", "kgs.h")]
+HEADERS = [os.path.join(CSRC, "kgs_internal.h"), os.path.join(CSRC, "kgs_nn.h"), os.path.join(CSRC, "kgs_tables.h"), os.path.join(CSRC, "kgs_ctx.h"), os.path.join(CSRC, "kgs_switch.h"), os.path.join(ROOT, "include", "kgs.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

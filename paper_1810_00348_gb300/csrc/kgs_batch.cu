@@ -434,8 +434,9 @@ int kgs_batch_solve(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
     int rc = kgs_batch_setup(&m, n, probs, &om);
     if (rc) return finish(rc);
     if (cudaSetDevice(m->dev) != cudaSuccess) return finish(KGS_ECUDA);
-    std::vector<int> nm(n, 0), stalled(n, 0), nd(n, 0);
-    std::vector<double> best(n, 1e300), last(n, -1.0);
+    std::vector<int> nm(n, 0), nd(n, 0);
+    std::vector<SolveSwitch> sw(n);
+    std::vector<double> last(n, -1.0);
     for (;;) {
         bool any = false;
         for (int i = 0; i < n; i++) any |= m->active[i] != 0;
@@ -448,14 +449,7 @@ int kgs_batch_solve(kgs_batch **out, int n, const kgs_problem *probs, const kgs_
             if (!m->active[i]) continue;
             nm[i] += count[i];
             const double r = last[i];
-            bool retire = r < opts->tol || nm[i] >= budget;
-            if (!retire) {
-                if (r < SOLVE_PROGRESS * best[i])
-                    stalled[i] = 0;
-                else if (++stalled[i] >= solve_patience(r))
-                    retire = true;
-                best[i] = std::min(best[i], r);
-            }
+            const bool retire = r < opts->tol || nm[i] >= budget || sw[i].stalled_after(r);
             if (retire) {
                 m->active[i] = 0;
                 m->dirty = true;

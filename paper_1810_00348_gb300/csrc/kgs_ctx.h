@@ -7,6 +7,7 @@
 
 #include <vector>
 
+#include "kgs_switch.h"
 #include "kgs_tables.h"
 
 struct kgs_ctx {
@@ -65,32 +66,6 @@ struct kgs_ctx {
 
 
 namespace kgs {
-
-// Switch rule of the mixed-then-FP64 solves: mixed iterations run in chunks;
-// an instance leaves the mixed phase once its residual has not fallen below
-// SOLVE_PROGRESS x its best value for solve_patience(r) chunks in a row.
-//  * r >= SOLVE_NEAR_FLOOR: twenty chunks (small-Kn solves can first rise for
-//    a while);
-//  * SOLVE_FLOOR_BAND <= r < SOLVE_NEAR_FLOOR: six chunks.  At small Kn the
-//    residual falls with bumps: a slowly damped oscillation of the iteration
-//    whose period is about 25 iterations (Kn 0.05 cavity: the residual rises
-//    from 3e-4 to 6e-4 and takes 20 iterations to fall back below its
-//    previous best), which two chunks mistook for the noise floor;
-//  * r < SOLVE_FLOOR_BAND: two chunks.  The mixed form's own floor (rounding
-//    noise of the smallest field, about 1e-6 with the deviation-form source)
-//    lies here, and there a stall is the floor.
-constexpr int SOLVE_CHUNK = 5;
-constexpr double SOLVE_PROGRESS = 0.9;
-constexpr double SOLVE_NEAR_FLOOR = 1e-3;
-constexpr double SOLVE_FLOOR_BAND = 3e-6;
-constexpr int SOLVE_PATIENCE_FAR = 20;
-constexpr int SOLVE_PATIENCE_MID = 6;
-constexpr int SOLVE_PATIENCE = 2;
-inline int solve_patience(double r)
-{
-    if (r >= SOLVE_NEAR_FLOOR) return SOLVE_PATIENCE_FAR;
-    return r >= SOLVE_FLOOR_BAND ? SOLVE_PATIENCE_MID : SOLVE_PATIENCE;
-}
 
 int cuda_err(cudaError_t e);
 

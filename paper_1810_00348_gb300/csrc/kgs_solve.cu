@@ -12,7 +12,7 @@
 // residual does not fall monotonically: it first rises for a while, and
 // later falls with bumps of about 25 iterations, so a stall counts as the
 // floor only after twenty chunks above 1e-3, six chunks down to 3e-6 and two
-// chunks below (kgs::solve_patience).  Leaving the mixed phase at a bump
+// chunks below (kgs::SolveSwitch).  Leaving the mixed phase at a bump
 // costs the FP64 iterations that the mixed form would have done about twenty
 // times faster.
 #include <cuda_runtime.h>
@@ -25,8 +25,6 @@
 namespace {
 
 using kgs::SOLVE_CHUNK;
-using kgs::SOLVE_PROGRESS;
-using kgs::solve_patience;
 
 kgs_opts opts_for(const kgs_problem *p, int precision, double tol, int max_iters, void *stream)
 {
@@ -65,20 +63,13 @@ extern "C" int kgs_solve(const kgs_problem *p, const double *initial, double tol
     if ((rc = kgs_setup(&m, &p->grid, p->solid, &p->vgrid, &p->gas, &p->bc, &om))) return finish(rc);
     if (initial && (rc = kgs_set_initial(m, initial))) return finish(rc);
     // mixed phase
-    double best = 1e300;
-    int stalled = 0;
+    kgs::SolveSwitch sw;
     while (n_mixed < max_iters) {
         int done = 0;
         rc = kgs_iterate(m, std::min(SOLVE_CHUNK, max_iters - n_mixed), &done, &r);
         n_mixed += done;
         if (rc) return finish(rc);
-        if (r < tol) break;
-        if (r < SOLVE_PROGRESS * best) {
-            stalled = 0;
-        } else if (++stalled >= solve_patience(r)) {
-            break;
-        }
-        best = std::min(best, r);
+        if (r < tol || sw.stalled_after(r)) break;
     }
     if (n_mixed >= max_iters && !(r < tol)) {
         // the budget ended in the mixed phase
