@@ -29,7 +29,12 @@
  * the stated number of elements.  The library allocates (cudaMalloc) and
  * frees all of its device memory itself and launches on the stream given in
  * kgs_opts (NULL = the legacy default stream) of the device that is current
- * at kgs_setup.  One context must not be used by two host threads at once;
+ * at kgs_setup.  Set-up calls (kgs_setup, kgs_batch_setup, kgs_net_create,
+ * kgs_net_set_params) copy their tables on the legacy default stream and
+ * wait for those copies before they return or launch, so a non-blocking
+ * stream needs no ordering by the caller; they may also wait for work the
+ * caller queued on the legacy default stream.  One context must not be used
+ * by two host threads at once;
  * distinct contexts are independent.  Results are deterministic: every
  * reduction runs in a fixed order.
  *

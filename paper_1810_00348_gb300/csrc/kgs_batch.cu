@@ -187,6 +187,10 @@ int rebuild(kgs_batch *b)
         KGS_CHECK(e);
         for (int i = 0; i < b->n; i++) swap_state(b->ctx[i]);
     }
+    // The work list, chain places and arguments (and, before the first
+    // rebuild, the set-up tables) were copied on the legacy default stream;
+    // the graphs run on the batch's stream, which need not wait for it.
+    KGS_CHECK(cudaStreamSynchronize(cudaStreamLegacy));
     // two swaps: every instance is back on its current buffers
     b->next = 0;
     b->dirty = false;

@@ -444,6 +444,8 @@ int kgs_net_create(kgs_net **out, int n_layers, const int *channels, unsigned lo
         cudaMemset(n->g, 0, off * 4) != cudaSuccess || cudaMemset(n->m1, 0, off * 4) != cudaSuccess ||
         cudaMemset(n->m2, 0, off * 4) != cudaSuccess)
         return fail(KGS_ECUDA);
+    // those ran on the legacy default stream; n->stream may not wait for it
+    if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) return fail(KGS_ECUDA);
     to_bf16_kernel<<<nblk(off, 256), 256, 0, n->stream>>>(n->p, off, n->pb);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(n->stream) != cudaSuccess) return fail(KGS_ECUDA);
     *out = n;
@@ -500,11 +502,15 @@ int kgs_net_set_params(kgs_net *n, const float *host)
     if (!n || !host) return KGS_EINVAL;
     std::vector<float> h(n->n_params, 0.f);
     unpack_unpadded(n, host, h.data());
+    NN_CHECK(cudaStreamSynchronize(n->stream));  // no kernel of the network still reads the parameters
     NN_CHECK(cudaMemcpy(n->p, h.data(), n->n_params * 4, cudaMemcpyHostToDevice));
-    to_bf16_kernel<<<nblk(n->n_params, 256), 256, 0, n->stream>>>(n->p, n->n_params, n->pb);
-    NN_CHECK(cudaGetLastError());
     NN_CHECK(cudaMemset(n->m1, 0, n->n_params * 4));
     NN_CHECK(cudaMemset(n->m2, 0, n->n_params * 4));
+    // the copy and the memsets ran on the legacy default stream; n->stream
+    // may not wait for it
+    NN_CHECK(cudaStreamSynchronize(cudaStreamLegacy));
+    to_bf16_kernel<<<nblk(n->n_params, 256), 256, 0, n->stream>>>(n->p, n->n_params, n->pb);
+    NN_CHECK(cudaGetLastError());
     n->step = 0;
     NN_CHECK(cudaStreamSynchronize(n->stream));
     return KGS_OK;

@@ -456,7 +456,11 @@ int kgs_setup(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, const k
     if (rc) return rc;
     (void)cudaGetLastError();  // launches below check their own status
     if ((rc = ctx_create(out, grid, solid, vg, gas, bc, opts))) return rc;
-    if ((rc = ctx_persist_init(*out))) {
+    rc = ctx_persist_init(*out);
+    // the persistent sweep's tables and the accumulator fill went to the
+    // legacy default stream as well
+    if (!rc && cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) rc = KGS_ECUDA;
+    if (rc) {
         kgs_destroy(*out);
         *out = nullptr;
     }
@@ -535,6 +539,10 @@ int kgs::ctx_create(kgs_ctx **out, const kgs_grid *grid, const uint8_t *solid, c
     c->ev.resize(2 * t.stage_n.size());
     for (auto &e : c->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(KGS_ECUDA);
+    // the uploads and memsets above ran on the legacy default stream, which a
+    // non-blocking stream of the caller does not wait for: complete them
+    // before the first kernel on c->stream reads the tables
+    if (cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) return fail(KGS_ECUDA);
     if ((rc = initial_state(c, nullptr))) return fail(rc);
     *out = c;
     return KGS_OK;
