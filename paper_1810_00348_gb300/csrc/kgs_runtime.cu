@@ -623,6 +623,7 @@ int kgs_close_sums(kgs_ctx *c, const double *sums_dev, double *residual)
 int kgs_moments(kgs_ctx *c, double *out)
 {
     if (!c || !out) return KGS_EINVAL;
+    KGS_CHECK(cudaSetDevice(c->dev));
     KGS_CHECK(cudaMemcpyAsync(out, c->mac, sizeof(double) * 8 * c->t.ncell, cudaMemcpyDeviceToHost, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     return KGS_OK;
@@ -631,6 +632,7 @@ int kgs_moments(kgs_ctx *c, double *out)
 int kgs_moments_device(kgs_ctx *c, double *out_dev)
 {
     if (!c || !out_dev) return KGS_EINVAL;
+    KGS_CHECK(cudaSetDevice(c->dev));
     KGS_CHECK(
         cudaMemcpyAsync(out_dev, c->mac, sizeof(double) * 8 * c->t.ncell, cudaMemcpyDeviceToDevice, c->stream));
     return KGS_OK;
@@ -639,6 +641,7 @@ int kgs_moments_device(kgs_ctx *c, double *out_dev)
 int kgs_rho_w(kgs_ctx *c, double *out)
 {
     if (!c || !out) return KGS_EINVAL;
+    KGS_CHECK(cudaSetDevice(c->dev));
     KGS_CHECK(cudaMemcpyAsync(out, c->rho_w, sizeof(double) * 6 * c->t.ncell, cudaMemcpyDeviceToHost, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     return KGS_OK;
@@ -647,6 +650,7 @@ int kgs_rho_w(kgs_ctx *c, double *out)
 int kgs_set_rho_w(kgs_ctx *c, const double *in)
 {
     if (!c || !in) return KGS_EINVAL;
+    KGS_CHECK(cudaSetDevice(c->dev));
     KGS_CHECK(cudaMemcpyAsync(c->rho_w, in, sizeof(double) * 6 * c->t.ncell, cudaMemcpyHostToDevice, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
     return KGS_OK;
@@ -670,6 +674,7 @@ int kgs_save(kgs_ctx *c, void *buf, size_t *len)
         return KGS_OK;
     }
     if (*len < need) return KGS_EINVAL;
+    KGS_CHECK(cudaSetDevice(c->dev));
     CkptHeader h{CKPT_MAGIC, c->t.nx, c->t.ny, c->t.nz, c->t.Nv, c->iteration, c->M0, c->last_residual};
     std::memcpy(buf, &h, sizeof h);
     double *body = reinterpret_cast<double *>(static_cast<char *>(buf) + sizeof h);
@@ -691,6 +696,7 @@ int kgs_load(kgs_ctx *c, const void *buf, size_t len)
     if (h.magic != CKPT_MAGIC || h.nx != c->t.nx || h.ny != c->t.ny || h.nz != c->t.nz || h.Nv != c->t.Nv)
         return KGS_EFORMAT;
     const double *body = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof h);
+    KGS_CHECK(cudaSetDevice(c->dev));
     KGS_CHECK(cudaMemcpyAsync(c->mac, body, sizeof(double) * 8 * n, cudaMemcpyHostToDevice, c->stream));
     KGS_CHECK(cudaMemcpyAsync(c->rho_w, body + 8 * n, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, c->stream));
     KGS_CHECK(cudaStreamSynchronize(c->stream));
