@@ -344,9 +344,12 @@ def run_ours(args, world, rank, local):
         cores = os.cpu_count() or 1
         if cores > 1:
             # the same sample on every host core (concurrent velocity ranges)
-            allc = time_oracle_sample(threads=cores)
-            if allc["cores"] > 1:
-                cpu["all_cores"] = {"value": allc["value"], "cores": allc["cores"], "sample": allc["sample"]}
+            try:
+                allc = time_oracle_sample(threads=cores)
+                if allc["cores"] > 1:
+                    cpu["all_cores"] = {"value": allc["value"], "cores": allc["cores"], "sample": allc["sample"]}
+            except Exception as e:  # noqa: BLE001 - reported in the JSON line
+                cpu["all_cores"] = {"error": repr(e)}
     line = {
         "metric": METRIC, "value": value, "unit": "phase-point updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
